@@ -1,0 +1,384 @@
+"""Benchmark of the finite-difference wave step on GB300.
+
+A bench step is one time step (Eq. 3) of the whole hot path over a 512^3
+single-precision grid: the radius-R stencil, leapfrog update, Cerjan layer,
+Ricker source and a 512 x 512 receiver plane, fused in one kernel launch.
+The default workload is the single large shot (512^3 layered model, radius 4,
+20-cell damping layer, 1000 steps per shot); radius 8 and the paper's VTI
+operator (R_xy = 12, R_z = 8) are selectable with --workload.
+
+Prints one JSON line.  `value` is grid-point updates per second with all
+inputs resident in HBM (three 512 MiB fields per shot: larger than L2, so no
+flush is needed between steps), timed with CUDA events on the grid's stream.
+`e2e` is one whole shot through the C ABI from pinned host memory: model
+upload, steps, receiver traces back to the host.  `roofline` compares the
+stencil kernel's algorithmic bytes per launch with the measured HBM copy
+bandwidth.  `cpu_baseline` times the FP64 CPU oracle on a bounded slab of the
+same workload.  `--impl reference` times only that oracle.
+
+Multi-GPU (torchrun, one rank per GPU): shots are independent, so each rank
+runs its own replica shot (weak scaling) and only the timing is reduced.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s & % of HBM roofline; shots/s and p50/p99 vs plain loop"
+UNIT = "grid-point updates/s"
+WORKLOADS = {
+    "iso512_r4": dict(mode="iso", R=4, bytes_per_pt=16, kernel="iso_sweep_kernel"),
+    "iso512_r8": dict(mode="iso", R=8, bytes_per_pt=16, kernel="iso_sweep_kernel"),
+    "vti512": dict(mode="vti", R=12, bytes_per_pt=36, kernel="vti_sweep_kernel"),
+}
+KERNEL_SRC = {"iso_sweep_kernel": "iso_sweep.cu", "vti_sweep_kernel": "vti_sweep.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="iso512_r4", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=512, help="grid points per axis")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch", default="", help="tx,ty,zchunk,lookahead override")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def make_shot(wl: str, n: int, seed: int, with_model=True):
+    from paper_1410_1387_gb300 import synth
+    w = WORKLOADS[wl]
+    if w["mode"] == "iso":
+        return synth.layered_shot(n, w["R"], nsteps=1000, seed=seed, with_model=with_model)
+    return synth.vti_shot(n, nsteps=1000, seed=seed, with_model=with_model)
+
+
+def workload_config(wl, shot, args):
+    w = WORKLOADS[wl]
+    return {
+        "workload": f"{wl}_layered" if w["mode"] == "iso" else "vti512_r12_8_layered",
+        "grid": [shot.nx, shot.ny, shot.nz],
+        "operator": "isotropic acoustic" if w["mode"] == "iso" else "VTI pseudo-acoustic (Eqs. 1-2)",
+        "radius": [shot.r_xy, shot.r_z],
+        "steps_per_shot": shot.nsteps,
+        "damping_layer_cells": shot.nb,
+        "receivers": int(len(shot.receivers)),
+        "model": "10-layer velocity 1500-4500 m/s, +-5% cell noise, seeded",
+        "l2": "no flush: every step reads >= 1.5 GiB of inputs (> 129 MB L2)",
+        "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), float(p[3]), p[4], p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[4]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded slab of the same workload)
+# ---------------------------------------------------------------------------
+
+def oracle_slab_problem(shot, nzs):
+    import oracle.oracle as O
+    v = shot.v[:nzs] if shot.v is not None else None
+    kw = dict(r_xy=shot.r_xy, r_z=shot.r_z, h=shot.h, dt=shot.dt, nb=shot.nb, sponge_a=shot.sponge_a,
+              src=(shot.src[0], shot.src[1], min(shot.src[2], nzs - 1)))
+    if shot.mode == "vti":
+        kw["dzk"] = shot.dzk[:nzs - 1]
+    return O.Problem(shot.nx, shot.ny, nzs, **kw), v
+
+
+def time_oracle(shot, seconds: float, steps: int | None = None, warmup: int = 0):
+    """Oracle points/s on a (nx, ny, nzs) slab.  Returns (pts_per_s, detail)."""
+    import oracle.oracle as O
+    nzs = 2
+    while True:
+        P, v = oracle_slab_problem(shot, nzs)
+        args = (v, shot.eps[:nzs], shot.delta[:nzs]) if shot.mode == "vti" else (v,)
+        t0 = time.perf_counter()
+        (P.vti_run if shot.mode == "vti" else P.iso_run)(*args, 1, traces=False)
+        dt1 = time.perf_counter() - t0
+        per_step_budget = seconds / (steps + warmup) if steps else seconds / 5
+        if dt1 * 2 > per_step_budget or nzs >= shot.nz:
+            break
+        nzs = min(shot.nz, nzs * 2)
+    nsteps = steps if steps else max(1, int(seconds / max(dt1, 1e-6)))
+    state = None
+    if warmup:
+        out = (P.vti_run if shot.mode == "vti" else P.iso_run)(*args, warmup, traces=False)
+        state = out
+    t0 = time.perf_counter()
+    if shot.mode == "vti":
+        kw = {} if state is None else dict(p=state[0], pprev=state[1], q=state[2], qprev=state[3])
+        P.vti_run(*args, nsteps, traces=False, n0=warmup, **kw)
+    else:
+        kw = {} if state is None else dict(u=state[0], uprev=state[1])
+        P.iso_run(*args, nsteps, traces=False, n0=warmup, **kw)
+    el = time.perf_counter() - t0
+    pts = shot.nx * shot.ny * nzs
+    return pts * nsteps / el, {"cores": O.num_threads(), "slab": [shot.nx, shot.ny, nzs], "steps": nsteps,
+                               "seconds": el}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# traffic recorded by ncu (profiles/), valid while the kernel source is unchanged
+# ---------------------------------------------------------------------------
+
+def kernel_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in (KERNEL_SRC[kernel], "ptx.cuh", "fd_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1410_1387_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(wl: str, kernel: str, n: int):
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{wl}.md")
+    if not os.path.exists(path) or n != 512:
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernel_hash(kernel):
+        return None
+    return float(m.group(1))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    shot = make_shot(args.workload, args.n, seed=1)
+    budget = 150.0
+    pts_s, det = time_oracle(shot, budget, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": pts_s, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * det["seconds"] / det["steps"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.workload, shot, args),
+        "cpu_baseline": {"value": pts_s, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                         "sample": f"FP64 C oracle, {det['steps']} steps of a {det['slab']} slab of the "
+                                   f"workload's model", "cpu": cpu_model()},
+        "e2e": {"value": pts_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1410_1387_gb300 import fd
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    shot = make_shot(args.workload, args.n, seed=1 + rank)
+    K, W = args.steps, args.warmup
+    pts = shot.nx * shot.ny * shot.nz
+
+    # ---- device-resident timing -------------------------------------------------
+    g = fd.grid_from_shot(shot, device=dev, nt_cap=K + W)
+    if args.launch:
+        g.set_launch(*[int(x) for x in args.launch.split(",")])
+    stream = g.stream
+    g.run(W)
+    g.sync()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        g.run(K)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    g.sync()
+    el_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    value = pts * K * world / (el_ms * 1e-3)
+    launch_ms = el_ms / K
+
+    # ---- end to end: one shot through the C ABI from pinned host memory -------------
+    e2e = None
+    if not args.no_e2e:
+        nsh = shot.nsteps
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        v_h = pin(shot.v)
+        eps_h = pin(shot.eps) if shot.mode == "vti" else None
+        del_h = pin(shot.delta) if shot.mode == "vti" else None
+        tr_h = torch.empty((nsh, len(shot.receivers)), dtype=torch.float32).pin_memory()
+        spec = fd.GridSpec.from_shot(shot)
+        g = fd.Grid(spec, device=dev)
+        g.add_source(*shot.src, freq_hz=shot.src_f, t0=shot.src_t0, amp=shot.src_amp)
+        g.set_receivers(shot.receivers, nsh)
+        if args.launch:
+            g.set_launch(*[int(x) for x in args.launch.split(",")])
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.device(dev):
+            fd.fd_set_model(g.h, v_h.data_ptr(), eps_h.data_ptr() if eps_h is not None else None,
+                            del_h.data_ptr() if del_h is not None else None, fd.FD_PTR_HOST)
+            fd.fd_run(g.h, nsh)
+            fd.fd_read_receivers(g.h, 0, nsh, tr_h.data_ptr(), fd.FD_PTR_HOST)
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        g.close()
+        nmodel = 3 if shot.mode == "vti" else 1
+        e2e = {"value": pts * nsh * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": nmodel * pts * 4 / nsh,
+               "d2h_bytes_per_step": len(shot.receivers) * 4,
+               "shot_seconds": e2e_s, "steps_per_shot": nsh}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peak()
+    algo = w["bytes_per_pt"] * pts
+    achieved = algo / (launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(args.workload, w["kernel"], args.n),
+            "kernel": w["kernel"], "algorithmic_bytes_per_launch": algo,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        pts_s, det = time_oracle(shot, args.cpu_seconds)
+        cpu = {"value": pts_s, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+               "sample": f"FP64 C oracle, {det['steps']} steps of a {det['slab']} slab of the same model",
+               "cpu": cpu_model()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": el_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_config(args.workload, shot, args),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
+        "clocks": clk.summary(), "impl": "ours",
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import __graft_entry__
+    __graft_entry__.build()
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * fd.h -- C ABI of the GB300 finite-difference wave-propagation library (libfd.so).
+ *
+ * One explicit time step of the high-order central finite-difference wave
+ * equation of Medina, St-Cyr & Warburton, "High-Order Finite-differences on
+ * multi-threaded architectures using OCCA" (arXiv 1410.1387):
+ *   - the centred leapfrog of Sec. 1, Eq. 3:  u^{n+1} = 2u^n - u^{n-1} + dt^2 F(u^n);
+ *   - F for the isotropic acoustic case: v^2 (d_xx + d_yy + d_zz) u + s(t) delta;
+ *   - F for the VTI pseudo-acoustic system of Eqs. 1-2 (p, q fields, velocities
+ *     nu_x = nu_z sqrt(1+2 eps), nu_n = nu_z sqrt(1+2 delta));
+ *   - the symmetric x-y stencil of radius R_xy (Eq. 4) and the per-plane z
+ *     stencil of radius R_z (Eq. 5, variable dz_k absorbed into the weights);
+ *   - the Ricker source of Sec. 1 (f = 15 Hz in the paper), the Cerjan damping
+ *     layer and the zero halo beyond the grid (Sec. 1, last paragraph);
+ *   - receivers sampling the new level every step (an addition: the paper has
+ *     no receivers; seismic imaging needs them).
+ *
+ * Conventions
+ *   Every call returns an int status: FD_OK (0) or a negative FD_ERR_* code.
+ *   fd_last_error() gives a message for the calling thread's last failure.
+ *   No call throws, exits or aborts.  All calls are thread-compatible, not
+ *   thread-safe: one grid must not be used from two threads at once.
+ *
+ * Layout
+ *   Fields are single precision, x fastest: element (i, j, k) sits at
+ *   i + pitch*(j + ny*k), pitch = fd_layout().pitch (a multiple of 32 floats,
+ *   so every row starts on a 128-byte boundary).  Dense arrays passed in or
+ *   out of the library (models, states) have pitch nx instead.
+ *   Points outside 0..n-1 on any axis hold the value zero (the zero halo).
+ *
+ * Ownership
+ *   The caller owns all large device memory: it allocates one device arena of
+ *   fd_required_bytes() bytes (256-byte aligned) and the receiver trace buffer,
+ *   and keeps both alive until fd_destroy_grid().  The library allocates only
+ *   small tables (weights, damping profiles, source samples, receiver indices,
+ *   a 64-byte device status block) and frees them in fd_destroy_grid().
+ *   All device work is ordered on the stream given to fd_create_grid()
+ *   (a cudaStream_t; NULL = the legacy default stream).  Calls that return
+ *   data to the host (fd_read_receivers to host memory, fd_get_state to host
+ *   memory, fd_sync, fd_set_model) synchronise that stream.
+ */
+#ifndef FD_H
+#define FD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FD_OK                0
+#define FD_ERR_INVALID_ARG  (-1)   /* bad size, radius, pointer, index, model value */
+#define FD_ERR_UNSTABLE_DT  (-2)   /* dt above the leapfrog stability bound */
+#define FD_ERR_OUT_OF_RANGE (-3)   /* receiver rows / steps beyond the buffers */
+#define FD_ERR_BAD_STATE    (-4)   /* call out of order (e.g. step before model) */
+#define FD_ERR_CUDA         (-5)   /* a CUDA runtime call failed */
+#define FD_ERR_TIMEOUT      (-6)   /* a device-side bounded wait gave up */
+#define FD_ERR_NO_MEMORY    (-7)   /* arena too small, or a small table allocation failed */
+#define FD_ERR_UNSUPPORTED  (-8)   /* radius / mode combination not compiled in */
+
+/* ---- enums ------------------------------------------------------------- */
+#define FD_MODE_ISO    0           /* isotropic acoustic, one field u */
+#define FD_MODE_VTI    1           /* VTI pseudo-acoustic, fields p and q (Eqs. 1-2) */
+#define FD_PTR_HOST    0
+#define FD_PTR_DEVICE  1
+
+typedef struct fd_grid fd_grid_t;  /* opaque handle */
+
+/* Problem description (Sec. 1: grid, spacings, radii, time step, damping). */
+typedef struct fd_desc {
+    int mode;             /* FD_MODE_ISO or FD_MODE_VTI */
+    int nx, ny, nz;       /* points per axis, >= 1 each; the damping layer is inside */
+    int r_xy;             /* x-y radius R_xy of Eq. 4: ISO 4 or 8, VTI 12 */
+    int r_z;              /* z radius R_z of Eq. 5: ISO == r_xy, VTI 8 */
+    double h;             /* dx = dy (> 0) */
+    double dz;            /* uniform dz (> 0), used when dz_k == NULL */
+    const double *dz_k;   /* VTI only, optional: nz-1 plane spacings (host; copied).
+                             Ghost planes beyond the grid continue the end spacing. */
+    double dt;            /* time step (> 0) */
+    int sponge_width;     /* Cerjan layer width in cells on every face; 0 = none */
+    double sponge_a;      /* Cerjan constant a: factor exp(-(a d)^2) per axis, d = 1..width */
+} fd_desc;
+
+/* Memory layout chosen for a description. */
+typedef struct fd_layout_t {
+    int pitch;            /* floats per row of every field */
+    int nfields;          /* wavefield buffers: ISO 2, VTI 4 */
+    int nmodel;           /* model buffers: ISO 1 (kappa), VTI 3 (kappa_x, kappa_n, kappa_z) */
+    size_t field_bytes;   /* bytes of one field buffer (pitch*ny*nz*4, rounded to 256) */
+    size_t arena_bytes;   /* (nfields + nmodel) * field_bytes */
+} fd_layout_t;
+
+/* Bytes of device arena that fd_create_grid() needs for d.  Pure host call. */
+int fd_required_bytes(const fd_desc *d, size_t *bytes);
+
+/* Pitch and buffer split for d.  Pure host call. */
+int fd_layout(const fd_desc *d, fd_layout_t *out);
+
+/*
+ * Largest stable dt for d with maximum velocity vmax (ISO: v; VTI: nu_z) and,
+ * for VTI, the maximum eps.  The bound is (v dt)^2 * rho <= 4 with rho the
+ * Gershgorin bound of the discrete operator's spectrum (exact for uniform
+ * spacing: rho = 2 sigma_xy / h^2 + sigma_z / dz^2, sigma = the stencil's
+ * symbol at the Nyquist frequency).  d->dt is ignored.  Pure host call.
+ */
+int fd_stability_limit(const fd_desc *d, double vmax, double eps_max, double *dt_max);
+
+/*
+ * Create a grid on `arena` (device memory of at least fd_required_bytes(d),
+ * 256-byte aligned, owned by the caller) ordered on `stream` (cudaStream_t).
+ * Zero-fills the wavefields (u^0 = u^{-1} = 0, the paper's quiescent start)
+ * and uploads the weight and damping tables.  The current CUDA device must be
+ * the one that owns the arena.  Time index starts at 0.
+ */
+int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stream,
+                   fd_grid_t **out);
+
+/*
+ * Set the model from dense nz x ny x nx float arrays (pitch nx), host or
+ * device per ptr_kind.  ISO: vz = velocity, eps = delta = NULL.  VTI: vz =
+ * nu_z, eps, delta = Thomsen parameters (Sec. 1).  Stores kappa = (v dt)^2
+ * (VTI: kappa_z = (nu_z dt)^2, kappa_x = kappa_z (1+2 eps), kappa_n =
+ * kappa_z (1+2 delta)), computed in double and rounded to float.
+ * Errors: FD_ERR_INVALID_ARG for a non-finite or non-positive velocity, or
+ * (VTI) eps < delta somewhere (the operator is unstable there: the paper's
+ * "eps - delta <= 0" is read as eps >= delta) or 1 + 2 delta <= 0;
+ * FD_ERR_UNSTABLE_DT when dt exceeds fd_stability_limit() for the model's
+ * maxima.  On error the grid has no model.  Synchronises the stream.
+ */
+int fd_set_model(fd_grid_t *g, const float *vz, const float *eps, const float *delta,
+                 int ptr_kind);
+
+/*
+ * Ricker point source (Sec. 1) at cell (ix, iy, iz): step n adds
+ *   dt^2 * amp * s(n dt - t0) / V,  s(t) = (1 - 2 pi^2 f^2 t^2) exp(-pi^2 f^2 t^2),
+ * to the new level of p (ISO: u), and of q too when inject_q != 0 (VTI only).
+ * V = h*h*dz (VTI with dz_k: h*h times the mean of the two spacings beside iz).
+ * A grid has one source; a second call replaces it.
+ */
+int fd_add_source(fd_grid_t *g, int ix, int iy, int iz, double freq_hz, double t0, double amp,
+                  int inject_q);
+
+/* As fd_add_source() with an arbitrary wavelet: step n adds dt^2 * s[n] / V
+   for n < nt (host array, copied), nothing after. */
+int fd_add_source_series(fd_grid_t *g, int ix, int iy, int iz, const float *s, int nt,
+                         int inject_q);
+
+/*
+ * Receivers at cells idx_xyz[3r..3r+2] (host ints, copied), r < nrec.  After
+ * the step that makes level n+1, trace_dev[(n - n_set) * nrec + r] = p^{n+1}
+ * (ISO: u^{n+1}) at receiver r, where n_set is the time index at this call.
+ * trace_dev is device memory of nt_cap * nrec floats owned by the caller.
+ * A set that is a row-major lattice on one z plane is sampled inside the
+ * stencil kernel; any other set by a small gather kernel after each step.
+ * nrec = 0 removes the receivers.
+ */
+int fd_set_receivers(fd_grid_t *g, const int *idx_xyz, int nrec, float *trace_dev, int nt_cap);
+
+/* One time step (Eq. 3): enqueue one stencil launch.  FD_ERR_BAD_STATE without
+   a model; FD_ERR_OUT_OF_RANGE if the receiver buffer is full. */
+int fd_step(fd_grid_t *g);
+
+/* nsteps time steps (one launch each, or replays of a captured CUDA graph, see
+   fd_set_graph).  Checks all of them against the receiver buffer first. */
+int fd_run(fd_grid_t *g, int nsteps);
+
+/* Use replays of a CUDA graph of `steps` launches (even, 2..1024) in fd_run;
+   0 = plain launches (the default). */
+int fd_set_graph(fd_grid_t *g, int steps);
+
+/*
+ * Copy receiver rows [t_begin, t_begin + t_count) (row m = step n_set + m) to
+ * dst (t_count * nrec floats, host or device per dst_kind).  Host copies
+ * synchronise the stream and report device-side errors.  FD_ERR_OUT_OF_RANGE
+ * for rows not written yet.
+ */
+int fd_read_receivers(fd_grid_t *g, int t_begin, int t_count, float *dst, int dst_kind);
+
+/*
+ * Copy the stored state out as dense nz x ny x nx arrays (any pointer may be
+ * NULL).  cur = u^n (VTI: p^n), prev = the stored older level, q_cur / q_prev
+ * the same for q (VTI).  The older level is stored before its second damping
+ * factor: with the Cerjan layer, the physical u^{n-1} is G * prev (G = 1
+ * outside the layer), which is how the sweep applies both factors in one pass.
+ * *time_index (may be NULL) receives n.  Synchronises for host destinations.
+ */
+int fd_get_state(fd_grid_t *g, float *cur, float *prev, float *q_cur, float *q_prev,
+                 int ptr_kind, int *time_index);
+
+/* Overwrite the stored state from dense arrays (same convention as
+   fd_get_state; NULL = leave that level unchanged) and set the time index. */
+int fd_set_state(fd_grid_t *g, const float *cur, const float *prev, const float *q_cur,
+                 const float *q_prev, int ptr_kind, int time_index);
+
+/* Device pointer and pitch of a stored level: which = 0 cur, 1 prev,
+   2 q_cur, 3 q_prev (VTI).  Valid until the next step. */
+int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch);
+
+/*
+ * Tile and pipeline of the stencil kernel (a tuning knob; results do not
+ * depend on it).  tx x ty points per CTA (tx a multiple of 4), zchunk planes
+ * per CTA, `lookahead` staged planes in flight.  A (tx, ty, lookahead)
+ * combination that is not built into the library returns FD_ERR_UNSUPPORTED
+ * and leaves the previous configuration in place.
+ */
+int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead);
+
+/* Current time index n (host-side count of enqueued steps). */
+int fd_time_index(fd_grid_t *g, int *n);
+
+/* Wait for the grid's stream; FD_ERR_TIMEOUT if a kernel's bounded wait gave up. */
+int fd_sync(fd_grid_t *g);
+
+/* Release the grid and its small tables (not the caller's arena or traces). */
+int fd_destroy_grid(fd_grid_t *g);
+
+/* Copy the calling thread's last error message into buf (always terminated). */
+int fd_last_error(char *buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FD_H */

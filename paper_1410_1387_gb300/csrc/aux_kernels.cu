@@ -1,0 +1,131 @@
+// Small kernels around the sweep: model conversion (Sec. 1's velocities to the
+// kappa arrays the step multiplies by), and the receiver gather for receiver
+// sets that are not a lattice on one plane.
+#include <math.h>
+
+#include "fd_internal.h"
+
+namespace fdk {
+
+// Positive floats order like their bit patterns, so atomicMax on the bits is a
+// float max for non-negative values.
+__device__ __forceinline__ void atomic_max_pos(unsigned int *addr, float v)
+{
+    if (v > 0.f) atomicMax(addr, __float_as_uint(v));
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned warp_sum(unsigned v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One block per (row j, plane k); threads stride over x.  `src_pitch` is nx for
+// dense input or the field pitch when the input was copied in place.
+__global__ void model_iso_kernel(const float *v, long long src_pitch, float *kappa, int nx,
+                                 int ny, long long pitch, double dt, DevState *st)
+{
+    const int j = blockIdx.x, k = blockIdx.y;
+    const float *vr = v + ((long long)k * ny + j) * src_pitch;
+    float *kr = kappa + ((long long)k * ny + j) * pitch;
+    float vmax = 0.f;
+    unsigned bad = 0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const float vv = vr[i];
+        if (!(vv > 0.f) || !isfinite(vv)) ++bad;
+        else vmax = fmaxf(vmax, vv);
+        const double vd = (double)vv * dt;
+        kr[i] = (float)(vd * vd);
+    }
+    vmax = warp_max(vmax);
+    bad = warp_sum(bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(reinterpret_cast<unsigned int *>(&st->vmax), vmax);
+        if (bad) atomicAdd(&st->bad, bad);
+    }
+}
+
+__global__ void model_vti_kernel(const float *vz, const float *eps, const float *delta,
+                                 long long src_pitch, float *kx, float *kn, float *kz, int nx,
+                                 int ny, long long pitch, double dt, DevState *st)
+{
+    const int j = blockIdx.x, k = blockIdx.y;
+    const long long so = ((long long)k * ny + j) * src_pitch;
+    const long long dof = ((long long)k * ny + j) * pitch;
+    float vmax = 0.f, kxmax = 0.f;
+    unsigned bad = 0, eld = 0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const float v = vz[so + i], e = eps[so + i], d = delta[so + i];
+        if (!(v > 0.f) || !isfinite(v) || !isfinite(e) || !isfinite(d) || !(1.0f + 2.0f * d > 0.f))
+            ++bad;
+        else
+            vmax = fmaxf(vmax, v);
+        if (e < d) ++eld;
+        const double vd = (double)v * dt;
+        const double k2 = vd * vd;
+        const double kxd = k2 * (1.0 + 2.0 * (double)e);
+        kz[dof + i] = (float)k2;
+        kx[dof + i] = (float)kxd;
+        kn[dof + i] = (float)(k2 * (1.0 + 2.0 * (double)d));
+        if (isfinite(kxd)) kxmax = fmaxf(kxmax, (float)kxd);
+    }
+    vmax = warp_max(vmax);
+    kxmax = warp_max(kxmax);
+    bad = warp_sum(bad);
+    eld = warp_sum(eld);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(reinterpret_cast<unsigned int *>(&st->vmax), vmax);
+        atomic_max_pos(reinterpret_cast<unsigned int *>(&st->kxmax), kxmax);
+        if (bad) atomicAdd(&st->bad, bad);
+        if (eld) atomicAdd(&st->eps_lt_delta, eld);
+    }
+}
+
+// Receiver gather: after the step that made level n+1 (the time index on the
+// device is then n+1), row n - t0 of the trace receives the field at idx.
+__global__ void gather_kernel(const float *field, long long pitch, long long plane, const int *idx,
+                              int nrec, float *trace, int t0, int cap, const DevState *st)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrec) return;
+    const int row = *reinterpret_cast<const volatile int *>(&st->step) - 1 - t0;
+    if (row < 0 || row >= cap) return;
+    const int i = idx[3 * r], j = idx[3 * r + 1], k = idx[3 * r + 2];
+    trace[(long long)row * nrec + r] = field[(long long)k * plane + (long long)j * pitch + i];
+}
+
+cudaError_t launch_model_iso(const float *v, long long src_pitch, float *kappa, int nx, int ny,
+                             int nz, long long pitch, double dt, DevState *st, cudaStream_t s)
+{
+    dim3 grid(ny, nz);
+    model_iso_kernel<<<grid, 128, 0, s>>>(v, src_pitch, kappa, nx, ny, pitch, dt, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_model_vti(const float *vz, const float *eps, const float *delta,
+                             long long src_pitch, float *kx, float *kn, float *kz, int nx, int ny,
+                             int nz, long long pitch, double dt, DevState *st, cudaStream_t s)
+{
+    dim3 grid(ny, nz);
+    model_vti_kernel<<<grid, 128, 0, s>>>(vz, eps, delta, src_pitch, kx, kn, kz, nx, ny, pitch, dt,
+                                          st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const float *field, long long pitch, long long plane, const int *idx,
+                          int nrec, float *trace, int t0, int cap, const DevState *st,
+                          cudaStream_t s)
+{
+    if (nrec <= 0) return cudaSuccess;
+    gather_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(field, pitch, plane, idx, nrec, trace, t0, cap,
+                                                     st);
+    return cudaGetLastError();
+}
+
+}  // namespace fdk

@@ -1,0 +1,757 @@
+// C ABI of libfd.so (include/fd.h): validation, layout, tables, launches,
+// graphs, state and receiver copies.  Every step of the time loop runs in the
+// CUDA kernels of iso_sweep.cu / vti_sweep.cu; this file only orders them.
+#include "fd.h"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "coeffs.h"
+#include "fd_internal.h"
+
+using namespace fdk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();   // clear a non-sticky error
+    return fail(FD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int get_encode()
+{
+    if (g_encode) return FD_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(FD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return FD_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int check_desc(const fd_desc *d)
+{
+    if (!d) return fail(FD_ERR_INVALID_ARG, "desc is NULL");
+    if (d->mode != FD_MODE_ISO && d->mode != FD_MODE_VTI) return fail(FD_ERR_INVALID_ARG, "bad mode %d", d->mode);
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1)
+        return fail(FD_ERR_INVALID_ARG, "grid %d x %d x %d: every axis needs >= 1 point", d->nx, d->ny, d->nz);
+    if (d->nx > (1 << 20) || d->ny > (1 << 20) || d->nz > (1 << 20))
+        return fail(FD_ERR_INVALID_ARG, "grid axis above 2^20 points");
+    if (!finite_pos(d->h) || !finite_pos(d->dt)) return fail(FD_ERR_INVALID_ARG, "h and dt must be finite and > 0");
+    if (!d->dz_k && !finite_pos(d->dz)) return fail(FD_ERR_INVALID_ARG, "dz must be finite and > 0");
+    if (d->sponge_width < 0 || !(d->sponge_a >= 0.0) || !std::isfinite(d->sponge_a))
+        return fail(FD_ERR_INVALID_ARG, "bad damping layer (width %d, a %g)", d->sponge_width, d->sponge_a);
+    if (d->mode == FD_MODE_ISO) {
+        if (d->r_xy != d->r_z) return fail(FD_ERR_INVALID_ARG, "isotropic mode needs r_xy == r_z");
+        if (d->dz_k) return fail(FD_ERR_INVALID_ARG, "dz_k is a VTI option");
+        if (!iso_supported(d->r_xy)) return fail(FD_ERR_UNSUPPORTED, "isotropic radius %d not built (4, 8)", d->r_xy);
+    } else {
+        if (!vti_supported(d->r_xy, d->r_z))
+            return fail(FD_ERR_UNSUPPORTED, "VTI radii (%d, %d) not built ((12, 8), (4, 4))", d->r_xy, d->r_z);
+        if (d->dz_k) {
+            if (d->nz < 2) return fail(FD_ERR_INVALID_ARG, "dz_k needs nz >= 2");
+            for (int k = 0; k < d->nz - 1; ++k)
+                if (!finite_pos(d->dz_k[k])) return fail(FD_ERR_INVALID_ARG, "dz_k[%d] must be finite and > 0", k);
+        }
+    }
+    return FD_OK;
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void compute_layout(const fd_desc *d, fd_layout_t *L)
+{
+    L->pitch = (int)round_up((size_t)d->nx, 32);
+    L->nfields = d->mode == FD_MODE_ISO ? 2 : 4;
+    L->nmodel = d->mode == FD_MODE_ISO ? 1 : 3;
+    L->field_bytes = round_up((size_t)L->pitch * d->ny * d->nz * sizeof(float), 256);
+    L->arena_bytes = (size_t)(L->nfields + L->nmodel) * L->field_bytes;
+}
+
+Launch default_launch(const fd_desc *d)
+{
+    Launch L;
+    L.tx = 64;
+    L.ty = 16;
+    L.lookahead = 2;
+    // z chunks: enough CTAs for several waves over 152 SMs x 2 resident CTAs
+    const long tiles = (long)((d->nx + L.tx - 1) / L.tx) * ((d->ny + L.ty - 1) / L.ty);
+    const long want = 152L * 2 * 4;
+    long chunks = std::max(1L, (want + tiles - 1) / tiles);
+    int zc = (int)((d->nz + chunks - 1) / chunks);
+    zc = std::max(zc, std::min(d->nz, 32));
+    L.zchunk = zc;
+    return L;
+}
+
+}  // namespace
+
+struct fd_grid {
+    fd_desc d{};
+    std::vector<double> dzk;
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    fd_layout_t lay{};
+    char *arena = nullptr;
+    float *field[4] = {};        // ISO: u[0], u[1]; VTI: p[0], p[1], q[0], q[1]
+    float *model[3] = {};        // ISO: kappa; VTI: kx, kn, kz
+    int cur = 0;                 // buffer index holding u^n (p^n, q^n)
+    int n = 0;                   // host time index
+    bool model_set = false;
+    DevState *st = nullptr;      // device status block
+    DevState *st_host = nullptr; // pinned copy
+    float *gx = nullptr, *gy = nullptr, *gz = nullptr;
+    float *ztab = nullptr;
+    double zrow_max = 0.0;       // Gershgorin bound of the z operator (VTI)
+    double sig_xy = 0.0;         // Gershgorin bound of the 1D x-y operator (unit grid)
+    float w0 = 0.f, wxy[kMaxR + 1] = {}, wz[kMaxR + 1] = {};
+    // source
+    float *src_tab = nullptr;
+    int src_len = 0, sx = -1, sy = -1, sz = -1, into_q = 0;
+    // receivers
+    int nrec = 0, rec_t0 = 0, rec_cap = 0;
+    float *trace = nullptr;
+    bool lattice = false;
+    RecLattice lat{};
+    int *rec_idx = nullptr;
+    // launch
+    Launch L{};
+    CUtensorMap tm[2];
+    // graphs
+    int graph_steps = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void drop_graphs(fd_grid *g)
+{
+    for (auto &e : g->gexec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+}
+
+int make_tensor_maps(fd_grid *g)
+{
+    int rc = get_encode();
+    if (rc) return rc;
+    const fd_desc &d = g->d;
+    const int R = d.r_xy;
+    cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    cuuint64_t strides[2] = {(cuuint64_t)g->lay.pitch * 4, (cuuint64_t)g->lay.pitch * d.ny * 4};
+    cuuint32_t box[3] = {(cuuint32_t)(g->L.tx + 2 * R), (cuuint32_t)(g->L.ty + 2 * R), 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+        CUresult r = g_encode(&g->tm[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g->field[b], dims, strides,
+                              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return FD_OK;
+}
+
+int set_launch(fd_grid *g, const Launch &L)
+{
+    if (L.tx <= 0 || L.ty <= 0 || L.zchunk <= 0 || L.lookahead <= 0)
+        return fail(FD_ERR_INVALID_ARG, "bad launch configuration");
+    if ((g->d.ny + L.ty - 1) / L.ty > 65535 || (g->d.nz + L.zchunk - 1) / L.zchunk > 65535)
+        return fail(FD_ERR_INVALID_ARG, "launch grid too large");
+    const bool built = g->d.mode == FD_MODE_ISO ? iso_config_built(g->d.r_xy, L)
+                                                : vti_config_built(g->d.r_xy, g->d.r_z, L);
+    if (!built)
+        return fail(FD_ERR_UNSUPPORTED, "tile %d x %d, lookahead %d is not built for this radius", L.tx, L.ty,
+                    L.lookahead);
+    g->L = L;
+    drop_graphs(g);
+    return make_tensor_maps(g);
+}
+
+// Enqueue one time step on stream s (no host-side bookkeeping).
+cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
+{
+    const fd_desc &d = g->d;
+    Source src{g->src_tab, g->src_len, g->sx, g->sy, g->sz, g->into_q};
+    RecLattice rec = g->lat;
+    rec.on = (g->nrec > 0 && g->lattice) ? 1 : 0;
+    const long long pitch = g->lay.pitch, plane = (long long)g->lay.pitch * d.ny;
+    cudaError_t e;
+    float *newbuf;
+    if (d.mode == FD_MODE_ISO) {
+        IsoArgs a{};
+        a.prev = g->field[1 - cur];
+        a.cur = g->field[cur];
+        a.kappa = g->model[0];
+        a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
+        a.pitch = pitch; a.plane = plane;
+        a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
+        a.zchunk = g->L.zchunk;
+        a.w0 = g->w0;
+        std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
+        std::memcpy(a.wz, g->wz, sizeof a.wz);
+        a.src = src; a.rec = rec; a.st = g->st;
+        e = launch_iso(d.r_xy, g->L, g->tm[cur], a, s);
+        newbuf = a.prev;
+    } else {
+        VtiArgs a{};
+        a.pprev = g->field[1 - cur];
+        a.qprev = g->field[2 + (1 - cur)];
+        a.p = g->field[cur];
+        a.q = g->field[2 + cur];
+        a.kx = g->model[0]; a.kn = g->model[1]; a.kz = g->model[2];
+        a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
+        a.ztab = g->ztab;
+        a.pitch = pitch; a.plane = plane;
+        a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
+        a.zchunk = g->L.zchunk;
+        a.w0 = g->w0;
+        std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
+        a.src = src; a.rec = rec; a.st = g->st;
+        e = launch_vti(d.r_xy, d.r_z, g->L, g->tm[cur], a, s);
+        newbuf = a.pprev;
+    }
+    if (e != cudaSuccess) return e;
+    if (g->nrec > 0 && !g->lattice)
+        e = launch_gather(newbuf, pitch, plane, g->rec_idx, g->nrec, g->trace, g->rec_t0, g->rec_cap,
+                          g->st, s);
+    return e;
+}
+
+int check_ready(fd_grid *g, int nsteps)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (!g->model_set) return fail(FD_ERR_BAD_STATE, "no model: call fd_set_model first");
+    if (nsteps < 0) return fail(FD_ERR_INVALID_ARG, "negative step count");
+    if ((long long)g->n + nsteps > 0x7fffffffLL) return fail(FD_ERR_OUT_OF_RANGE, "time index overflow");
+    if (g->nrec > 0 && (long long)g->n + nsteps - g->rec_t0 > g->rec_cap)
+        return fail(FD_ERR_OUT_OF_RANGE, "receiver buffer holds %d rows; step %d would need row %lld",
+                    g->rec_cap, g->n + nsteps - 1, (long long)g->n + nsteps - 1 - g->rec_t0);
+    return FD_OK;
+}
+
+int check_dev_status(fd_grid *g)
+{
+    CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream), "status copy");
+    CU(cudaStreamSynchronize(g->stream), "stream synchronize");
+    if (g->st_host->err & kErrTmaTimeout)
+        return fail(FD_ERR_TIMEOUT, "a stencil CTA (%d) timed out waiting for a TMA copy", g->st_host->err_info - 1);
+    return FD_OK;
+}
+
+int upload(void **dst, const void *src, size_t bytes)
+{
+    if (*dst) {
+        cudaFree(*dst);
+        *dst = nullptr;
+    }
+    if (bytes == 0) return FD_OK;
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) {
+        *dst = nullptr;
+        cudaGetLastError();
+        return fail(FD_ERR_NO_MEMORY, "table allocation of %zu bytes failed", bytes);
+    }
+    CU(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "table upload");
+    return FD_OK;
+}
+
+double source_volume(const fd_grid *g, int iz)
+{
+    const fd_desc &d = g->d;
+    if (d.mode == FD_MODE_VTI && !g->dzk.empty()) {
+        const double lo = iz >= 1 ? g->dzk[iz - 1] : g->dzk[0];
+        const double hi = iz <= d.nz - 2 ? g->dzk[iz] : g->dzk[d.nz - 2];
+        return d.h * d.h * 0.5 * (lo + hi);
+    }
+    return d.h * d.h * d.dz;
+}
+
+int set_source_table(fd_grid *g, int ix, int iy, int iz, const std::vector<double> &s, int inject_q)
+{
+    const fd_desc &d = g->d;
+    if (ix < 0 || ix >= d.nx || iy < 0 || iy >= d.ny || iz < 0 || iz >= d.nz)
+        return fail(FD_ERR_INVALID_ARG, "source cell (%d, %d, %d) outside the grid", ix, iy, iz);
+    if (inject_q && d.mode != FD_MODE_VTI) return fail(FD_ERR_INVALID_ARG, "inject_q is a VTI option");
+    const double scale = d.dt * d.dt / source_volume(g, iz);
+    std::vector<float> tab(s.size());
+    for (size_t i = 0; i < s.size(); ++i) tab[i] = (float)(s[i] * scale);
+    int rc = upload(reinterpret_cast<void **>(&g->src_tab), tab.data(), tab.size() * sizeof(float));
+    if (rc) return rc;
+    g->src_len = (int)tab.size();
+    g->sx = ix; g->sy = iy; g->sz = iz;
+    g->into_q = inject_q ? 1 : 0;
+    drop_graphs(g);
+    return FD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_last_error(char *buf, size_t n)
+{
+    if (!buf || n == 0) return FD_ERR_INVALID_ARG;
+    std::snprintf(buf, n, "%s", g_err.c_str());
+    return FD_OK;
+}
+
+int fd_layout(const fd_desc *d, fd_layout_t *out)
+{
+    int rc = check_desc(d);
+    if (rc) return rc;
+    if (!out) return fail(FD_ERR_INVALID_ARG, "out is NULL");
+    compute_layout(d, out);
+    return FD_OK;
+}
+
+int fd_required_bytes(const fd_desc *d, size_t *bytes)
+{
+    fd_layout_t L;
+    int rc = fd_layout(d, &L);
+    if (rc) return rc;
+    if (!bytes) return fail(FD_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = L.arena_bytes;
+    return FD_OK;
+}
+
+int fd_stability_limit(const fd_desc *d, double vmax, double eps_max, double *dt_max)
+{
+    int rc = check_desc(d);
+    if (rc) return rc;
+    if (!dt_max || !finite_pos(vmax) || !std::isfinite(eps_max) || 1.0 + 2.0 * eps_max <= 0.0)
+        return fail(FD_ERR_INVALID_ARG, "bad stability-limit arguments");
+    double c[kMaxR + 1];
+    central_d2(d->r_xy, c);
+    const double sxy = row_abs_sum(c, d->r_xy);
+    double rho;
+    if (d->mode == FD_MODE_ISO) {
+        rho = 2.0 * sxy / (d->h * d->h) + sxy / (d->dz * d->dz);
+    } else {
+        std::vector<double> tab((size_t)d->nz * (2 * d->r_z + 1));
+        z_weights(d->nz, d->r_z, d->dz_k, d->dz, tab.data());
+        rho = (1.0 + 2.0 * std::max(0.0, eps_max)) * 2.0 * sxy / (d->h * d->h) +
+              z_row_abs_max(tab.data(), d->nz, d->r_z);
+    }
+    *dt_max = 2.0 / (vmax * std::sqrt(rho));
+    return FD_OK;
+}
+
+int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stream, fd_grid_t **out)
+{
+    int rc = check_desc(d);
+    if (rc) return rc;
+    if (!out) return fail(FD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    fd_layout_t lay;
+    compute_layout(d, &lay);
+    if (!arena) return fail(FD_ERR_INVALID_ARG, "arena is NULL");
+    if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return fail(FD_ERR_INVALID_ARG, "arena not 256-byte aligned");
+    if (arena_bytes < lay.arena_bytes)
+        return fail(FD_ERR_NO_MEMORY, "arena has %zu bytes, needs %zu", arena_bytes, lay.arena_bytes);
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, arena) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(FD_ERR_INVALID_ARG, "arena is not device memory");
+    }
+
+    fd_grid *g = new (std::nothrow) fd_grid;
+    if (!g) return fail(FD_ERR_NO_MEMORY, "host allocation failed");
+    g->d = *d;
+    if (d->dz_k) g->dzk.assign(d->dz_k, d->dz_k + d->nz - 1);
+    g->d.dz_k = nullptr;
+    if (g->d.dz_k == nullptr && !g->dzk.empty() && !finite_pos(g->d.dz)) g->d.dz = g->dzk[0];
+    g->stream = static_cast<cudaStream_t>(stream);
+    g->lay = lay;
+    g->arena = static_cast<char *>(arena);
+    cudaGetDevice(&g->dev);
+    for (int b = 0; b < lay.nfields; ++b) g->field[b] = reinterpret_cast<float *>(g->arena + b * lay.field_bytes);
+    for (int m = 0; m < lay.nmodel; ++m)
+        g->model[m] = reinterpret_cast<float *>(g->arena + (lay.nfields + m) * lay.field_bytes);
+
+    auto bail = [&](int code) {
+        fd_destroy_grid(g);
+        return code;
+    };
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g->st), sizeof(DevState));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "status block allocation"));
+    e = cudaMallocHost(reinterpret_cast<void **>(&g->st_host), sizeof(DevState));
+    if (e != cudaSuccess) return bail(cuda_fail(e, "pinned status allocation"));
+    e = cudaMemsetAsync(g->st, 0, sizeof(DevState), g->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "status clear"));
+    e = cudaMemsetAsync(g->arena, 0, (size_t)lay.nfields * lay.field_bytes, g->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "wavefield clear"));
+
+    // weights (Eq. 4 on x-y; Eq. 4 on z for the isotropic case, Eq. 5 for VTI)
+    double c[kMaxR + 1];
+    central_d2(d->r_xy, c);
+    g->sig_xy = row_abs_sum(c, d->r_xy);
+    const double h2 = d->h * d->h;
+    for (int l = 1; l <= d->r_xy; ++l) g->wxy[l] = (float)(c[l] / h2);
+    if (d->mode == FD_MODE_ISO) {
+        const double dz2 = d->dz * d->dz;
+        g->w0 = (float)(c[0] * (2.0 / h2 + 1.0 / dz2));
+        for (int l = 1; l <= d->r_z; ++l) g->wz[l] = (float)(c[l] / dz2);
+    } else {
+        g->w0 = (float)(2.0 * c[0] / h2);
+        const int nw = 2 * d->r_z + 1;
+        std::vector<double> tab((size_t)d->nz * nw);
+        z_weights(d->nz, d->r_z, g->dzk.empty() ? nullptr : g->dzk.data(), g->d.dz, tab.data());
+        g->zrow_max = z_row_abs_max(tab.data(), d->nz, d->r_z);
+        std::vector<float> tf(tab.begin(), tab.end());
+        rc = upload(reinterpret_cast<void **>(&g->ztab), tf.data(), tf.size() * sizeof(float));
+        if (rc) return bail(rc);
+    }
+    // damping profiles (Cerjan), padded to the pitch for 128-bit loads
+    std::vector<float> px(lay.pitch, 1.0f), py(d->ny), pz(d->nz);
+    for (int i = 0; i < d->nx; ++i) px[i] = (float)cerjan(i, d->nx, d->sponge_width, d->sponge_a);
+    for (int j = 0; j < d->ny; ++j) py[j] = (float)cerjan(j, d->ny, d->sponge_width, d->sponge_a);
+    for (int k = 0; k < d->nz; ++k) pz[k] = (float)cerjan(k, d->nz, d->sponge_width, d->sponge_a);
+    if ((rc = upload(reinterpret_cast<void **>(&g->gx), px.data(), px.size() * 4)) ||
+        (rc = upload(reinterpret_cast<void **>(&g->gy), py.data(), py.size() * 4)) ||
+        (rc = upload(reinterpret_cast<void **>(&g->gz), pz.data(), pz.size() * 4)))
+        return bail(rc);
+
+    rc = set_launch(g, default_launch(d));
+    if (rc) return bail(rc);
+    *out = g;
+    return FD_OK;
+}
+
+int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    Launch L{tx, ty, zchunk, lookahead};
+    Launch old = g->L;
+    int rc = set_launch(g, L);
+    if (rc) {
+        set_launch(g, old);
+        return rc;
+    }
+    return FD_OK;
+}
+
+int fd_set_model(fd_grid_t *g, const float *vz, const float *eps, const float *delta, int ptr_kind)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    const fd_desc &d = g->d;
+    const bool vti = d.mode == FD_MODE_VTI;
+    if (!vz || (vti && (!eps || !delta)) || (!vti && (eps || delta)))
+        return fail(FD_ERR_INVALID_ARG, vti ? "VTI needs vz, eps and delta" : "isotropic mode takes v only");
+    if (ptr_kind != FD_PTR_HOST && ptr_kind != FD_PTR_DEVICE) return fail(FD_ERR_INVALID_ARG, "bad ptr_kind");
+    g->model_set = false;
+    drop_graphs(g);
+    const long long pitch = g->lay.pitch;
+    const size_t row = (size_t)d.nx * 4, rows = (size_t)d.ny * d.nz;
+    CU(cudaMemsetAsync(reinterpret_cast<char *>(g->st) + offsetof(DevState, vmax), 0, 16, g->stream),
+       "status clear");
+    const float *in[3] = {vz, eps, delta};
+    long long src_pitch = d.nx;
+    if (ptr_kind == FD_PTR_HOST) {
+        // stage the dense inputs in the model buffers, then convert in place
+        float *stage[3] = {vti ? g->model[2] : g->model[0], g->model[0], g->model[1]};
+        for (int m = 0; m < (vti ? 3 : 1); ++m) {
+            CU(cudaMemcpy2DAsync(stage[m], pitch * 4, in[m], row, row, rows, cudaMemcpyHostToDevice, g->stream),
+               "model upload");
+            in[m] = stage[m];
+        }
+        src_pitch = pitch;
+    }
+    cudaError_t e;
+    if (!vti)
+        e = launch_model_iso(in[0], src_pitch, g->model[0], d.nx, d.ny, d.nz, pitch, d.dt, g->st, g->stream);
+    else
+        e = launch_model_vti(in[0], in[1], in[2], src_pitch, g->model[0], g->model[1], g->model[2], d.nx, d.ny,
+                             d.nz, pitch, d.dt, g->st, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "model kernel");
+    CU(cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream), "status copy");
+    CU(cudaStreamSynchronize(g->stream), "stream synchronize");
+    const DevState &s = *g->st_host;
+    if (s.bad) return fail(FD_ERR_INVALID_ARG, "%u model values are not finite / not positive", s.bad);
+    if (vti && s.eps_lt_delta)
+        return fail(FD_ERR_INVALID_ARG, "%u cells have eps < delta (the VTI system is unstable there)", s.eps_lt_delta);
+    const double dt = d.dt;
+    const double kmax = (double)s.vmax * dt * (double)s.vmax * dt;
+    double lam;
+    if (!vti) {
+        const double dz2 = d.dz * d.dz;
+        lam = kmax * (2.0 * g->sig_xy / (d.h * d.h) + g->sig_xy / dz2);
+    } else {
+        lam = (double)s.kxmax * 2.0 * g->sig_xy / (d.h * d.h) + kmax * g->zrow_max;
+    }
+    if (lam > 4.0 * (1.0 + 1e-9))
+        return fail(FD_ERR_UNSTABLE_DT, "dt = %g exceeds the stability bound (%.6g of it) for v_max = %g", dt,
+                    std::sqrt(lam / 4.0), (double)s.vmax);
+    g->model_set = true;
+    return FD_OK;
+}
+
+int fd_add_source(fd_grid_t *g, int ix, int iy, int iz, double freq_hz, double t0, double amp, int inject_q)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (!finite_pos(freq_hz) || !std::isfinite(t0) || !std::isfinite(amp))
+        return fail(FD_ERR_INVALID_ARG, "bad Ricker parameters");
+    // beyond t0 + 4/f the wavelet is below 1e-60 relative: the table stops there
+    const double tend = t0 + 4.0 / freq_hz;
+    const double nmax = std::ceil(tend / g->d.dt) + 1.0;
+    if (nmax > (double)(1 << 26)) return fail(FD_ERR_INVALID_ARG, "source table too long (t0 + 4/f >> dt)");
+    const int len = std::max(0, (int)nmax);
+    std::vector<double> s(len);
+    for (int n = 0; n < len; ++n) s[n] = amp * ricker(n * g->d.dt - t0, freq_hz);
+    return set_source_table(g, ix, iy, iz, s, inject_q);
+}
+
+int fd_add_source_series(fd_grid_t *g, int ix, int iy, int iz, const float *s, int nt, int inject_q)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (nt < 0 || (nt > 0 && !s)) return fail(FD_ERR_INVALID_ARG, "bad source series");
+    std::vector<double> v(s, s + nt);
+    return set_source_table(g, ix, iy, iz, v, inject_q);
+}
+
+int fd_set_receivers(fd_grid_t *g, const int *idx, int nrec, float *trace_dev, int nt_cap)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    drop_graphs(g);
+    if (nrec == 0) {
+        g->nrec = 0;
+        g->lattice = false;
+        return FD_OK;
+    }
+    if (nrec < 0 || !idx || !trace_dev || nt_cap < 0) return fail(FD_ERR_INVALID_ARG, "bad receiver arguments");
+    const fd_desc &d = g->d;
+    for (int r = 0; r < nrec; ++r) {
+        const int i = idx[3 * r], j = idx[3 * r + 1], k = idx[3 * r + 2];
+        if (i < 0 || i >= d.nx || j < 0 || j >= d.ny || k < 0 || k >= d.nz)
+            return fail(FD_ERR_INVALID_ARG, "receiver %d at (%d, %d, %d) outside the grid", r, i, j, k);
+    }
+    // lattice detection: one plane, row-major, constant strides
+    bool lat = true;
+    int rnx = 1;
+    while (rnx < nrec && idx[3 * rnx + 1] == idx[1]) ++rnx;
+    const int rny = nrec / rnx;
+    const int rsx = rnx > 1 ? idx[3] - idx[0] : 1;
+    const int rsy = rny > 1 ? idx[3 * rnx + 1] - idx[1] : 1;
+    if (rny * rnx != nrec || rsx <= 0 || rsy <= 0) lat = false;
+    for (int r = 0; lat && r < nrec; ++r) {
+        const int ry = r / rnx, rx = r % rnx;
+        if (idx[3 * r] != idx[0] + rx * rsx || idx[3 * r + 1] != idx[1] + ry * rsy || idx[3 * r + 2] != idx[2])
+            lat = false;
+    }
+    g->lattice = lat;
+    g->nrec = nrec;
+    g->trace = trace_dev;
+    g->rec_cap = nt_cap;
+    g->rec_t0 = g->n;
+    g->lat = RecLattice{};
+    if (lat) {
+        g->lat.trace = trace_dev;
+        g->lat.nrec = nrec;
+        g->lat.rk = idx[2];
+        g->lat.rx0 = idx[0];
+        g->lat.ry0 = idx[1];
+        g->lat.rsx = rsx;
+        g->lat.rsy = rsy;
+        g->lat.rnx = rnx;
+        g->lat.rny = rny;
+        g->lat.t0 = g->n;
+        g->lat.cap = nt_cap;
+    } else {
+        int rc = upload(reinterpret_cast<void **>(&g->rec_idx), idx, (size_t)nrec * 3 * sizeof(int));
+        if (rc) {
+            g->nrec = 0;
+            return rc;
+        }
+    }
+    return FD_OK;
+}
+
+int fd_step(fd_grid_t *g) { return fd_run(g, 1); }
+
+int fd_set_graph(fd_grid_t *g, int steps)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (steps != 0 && (steps < 2 || steps > 1024 || steps % 2))
+        return fail(FD_ERR_INVALID_ARG, "graph steps must be 0 or even in 2..1024");
+    drop_graphs(g);
+    g->graph_steps = steps;
+    return FD_OK;
+}
+
+int fd_run(fd_grid_t *g, int nsteps)
+{
+    int rc = check_ready(g, nsteps);
+    if (rc) return rc;
+    int left = nsteps;
+    const int K = g->graph_steps;
+    while (K > 0 && left >= K) {
+        cudaGraphExec_t &ge = g->gexec[g->cur];
+        if (!ge) {
+            if (!g->cap_stream) CU(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking), "stream create");
+            CU(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t e = cudaSuccess;
+            for (int j = 0; j < K && e == cudaSuccess; ++j) e = enqueue_step(g, (g->cur + j) & 1, g->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+            if (e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(e, "step capture");
+            }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+            e = cudaGraphInstantiate(&ge, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                ge = nullptr;
+                return cuda_fail(e, "graph instantiate");
+            }
+        }
+        CU(cudaGraphLaunch(ge, g->stream), "graph launch");
+        g->n += K;   // K is even: the buffer parity is unchanged
+        left -= K;
+    }
+    for (; left > 0; --left) {
+        cudaError_t e = enqueue_step(g, g->cur, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step launch");
+        g->cur ^= 1;
+        g->n += 1;
+    }
+    return FD_OK;
+}
+
+int fd_read_receivers(fd_grid_t *g, int t_begin, int t_count, float *dst, int dst_kind)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (g->nrec == 0) return fail(FD_ERR_BAD_STATE, "no receivers");
+    if (t_begin < 0 || t_count < 0 || (t_count > 0 && !dst)) return fail(FD_ERR_INVALID_ARG, "bad read arguments");
+    if (dst_kind != FD_PTR_HOST && dst_kind != FD_PTR_DEVICE) return fail(FD_ERR_INVALID_ARG, "bad dst_kind");
+    const long long written = (long long)g->n - g->rec_t0;
+    if ((long long)t_begin + t_count > std::min<long long>(written, g->rec_cap))
+        return fail(FD_ERR_OUT_OF_RANGE, "rows [%d, %d) requested, %lld written", t_begin, t_begin + t_count, written);
+    const size_t bytes = (size_t)t_count * g->nrec * sizeof(float);
+    if (bytes)
+        CU(cudaMemcpyAsync(dst, g->trace + (size_t)t_begin * g->nrec, bytes,
+                           dst_kind == FD_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, g->stream),
+           "trace copy");
+    if (dst_kind == FD_PTR_HOST) return check_dev_status(g);
+    return FD_OK;
+}
+
+int fd_get_state(fd_grid_t *g, float *cur, float *prev, float *q_cur, float *q_prev, int ptr_kind, int *time_index)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (ptr_kind != FD_PTR_HOST && ptr_kind != FD_PTR_DEVICE) return fail(FD_ERR_INVALID_ARG, "bad ptr_kind");
+    const fd_desc &d = g->d;
+    if ((q_cur || q_prev) && d.mode != FD_MODE_VTI) return fail(FD_ERR_INVALID_ARG, "q is a VTI field");
+    float *dst[4] = {cur, prev, q_cur, q_prev};
+    const float *src[4] = {g->field[g->cur], g->field[1 - g->cur], g->field[2 + g->cur], g->field[3 - g->cur]};
+    const size_t row = (size_t)d.nx * 4;
+    for (int m = 0; m < 4; ++m)
+        if (dst[m])
+            CU(cudaMemcpy2DAsync(dst[m], row, src[m], (size_t)g->lay.pitch * 4, row, (size_t)d.ny * d.nz,
+                                 ptr_kind == FD_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                 g->stream),
+               "state copy");
+    if (time_index) *time_index = g->n;
+    if (ptr_kind == FD_PTR_HOST) return check_dev_status(g);
+    return FD_OK;
+}
+
+int fd_set_state(fd_grid_t *g, const float *cur, const float *prev, const float *q_cur, const float *q_prev,
+                 int ptr_kind, int time_index)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (ptr_kind != FD_PTR_HOST && ptr_kind != FD_PTR_DEVICE) return fail(FD_ERR_INVALID_ARG, "bad ptr_kind");
+    if (time_index < 0) return fail(FD_ERR_INVALID_ARG, "negative time index");
+    const fd_desc &d = g->d;
+    if ((q_cur || q_prev) && d.mode != FD_MODE_VTI) return fail(FD_ERR_INVALID_ARG, "q is a VTI field");
+    const float *src[4] = {cur, prev, q_cur, q_prev};
+    float *dst[4] = {g->field[g->cur], g->field[1 - g->cur], g->field[2 + g->cur], g->field[3 - g->cur]};
+    const size_t row = (size_t)d.nx * 4;
+    for (int m = 0; m < 4; ++m)
+        if (src[m])
+            CU(cudaMemcpy2DAsync(dst[m], (size_t)g->lay.pitch * 4, src[m], row, row, (size_t)d.ny * d.nz,
+                                 ptr_kind == FD_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                 g->stream),
+               "state copy");
+    g->st_host->step = time_index;
+    CU(cudaMemcpyAsync(&g->st->step, &g->st_host->step, sizeof(int), cudaMemcpyHostToDevice, g->stream),
+       "time index copy");
+    CU(cudaStreamSynchronize(g->stream), "stream synchronize");
+    g->n = time_index;
+    return FD_OK;
+}
+
+int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch)
+{
+    if (!g || !dev_ptr) return fail(FD_ERR_INVALID_ARG, "NULL argument");
+    if (which < 0 || which > 3 || (which > 1 && g->d.mode != FD_MODE_VTI)) return fail(FD_ERR_INVALID_ARG, "bad field");
+    const int b[4] = {g->cur, 1 - g->cur, 2 + g->cur, 3 - g->cur};
+    *dev_ptr = g->field[b[which]];
+    if (pitch) *pitch = g->lay.pitch;
+    return FD_OK;
+}
+
+int fd_time_index(fd_grid_t *g, int *n)
+{
+    if (!g || !n) return fail(FD_ERR_INVALID_ARG, "NULL argument");
+    *n = g->n;
+    return FD_OK;
+}
+
+int fd_sync(fd_grid_t *g)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    return check_dev_status(g);
+}
+
+int fd_destroy_grid(fd_grid_t *g)
+{
+    if (!g) return FD_OK;
+    if (g->stream || g->st) cudaStreamSynchronize(g->stream);
+    drop_graphs(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    void *bufs[] = {g->st, g->gx, g->gy, g->gz, g->ztab, g->src_tab, g->rec_idx};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (g->st_host) cudaFreeHost(g->st_host);
+    delete g;
+    cudaGetLastError();
+    return FD_OK;
+}
+
+}  // extern "C"

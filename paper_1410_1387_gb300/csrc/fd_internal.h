@@ -1,0 +1,109 @@
+// Internal declarations shared by the host side (fd_api.cpp) and the kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdk {
+
+constexpr int kMaxR = 12;          // largest stencil radius compiled in
+
+// Device-resident status block (64 bytes, library-allocated).
+struct DevState {
+    int step;               // time index n of the level u^n the next launch reads
+    unsigned int done;      // CTAs of the current launch that have read `step`
+    int err;                // bit flags, see kErr*
+    int err_info;           // 1 + linear CTA index of the first error
+    float vmax;             // model statistics written by the model kernels
+    float kxmax;
+    unsigned int bad;       // count of invalid model values
+    unsigned int eps_lt_delta;
+    int pad[8];
+};
+static_assert(sizeof(DevState) == 64, "status block size");
+constexpr int kErrTmaTimeout = 1;
+
+// Fused receiver lattice: a row-major rnx x rny lattice on plane rk.
+struct RecLattice {
+    float *trace;           // device, rows of nrec floats
+    long long nrec;         // rnx * rny
+    int on;                 // 1 when sampled inside the stencil kernel
+    int rk, rx0, ry0, rsx, rsy, rnx, rny;
+    int t0;                 // time index at which row 0 was defined
+    int cap;                // rows available
+};
+
+struct Source {
+    const float *tab;       // tab[n] = dt^2 * s(n) / V (float), n < len
+    int len;
+    int sx, sy, sz;         // cell; sx < 0 = no source
+    int into_q;             // VTI: add to q as well
+};
+
+// Arguments of the isotropic sweep (Eq. 3 with the Laplacian of Eq. 4 on all axes).
+struct IsoArgs {
+    float *prev;            // stored older level in, u^{n+1} out (in place)
+    const float *cur;       // u^n (plain loads for the first planes of a z chunk)
+    const float *kappa;     // (v dt)^2
+    const float *gx, *gy, *gz;  // damping factors per axis (1 outside the layer)
+    long long pitch;        // floats per row
+    long long plane;        // floats per plane
+    int nx, ny, nz;
+    int zchunk;             // planes per CTA
+    float w0;               // centre weight c0 (2/h^2 + 1/dz^2)
+    float wxy[kMaxR + 1];   // c_l / h^2
+    float wz[kMaxR + 1];    // c_l / dz^2
+    Source src;
+    RecLattice rec;
+    DevState *st;
+    unsigned int ncta;
+};
+
+// Arguments of the VTI sweep (Eqs. 1-2, 4-5).
+struct VtiArgs {
+    float *pprev, *qprev;   // stored older levels in, new levels out (in place)
+    const float *p, *q;     // p^n, q^n
+    const float *kx, *kn, *kz;
+    const float *gx, *gy, *gz;
+    const float *ztab;      // nz x (2 R_z + 1) z weights (dz absorbed)
+    long long pitch, plane;
+    int nx, ny, nz;
+    int zchunk;
+    float w0;               // 2 c0 / h^2
+    float wxy[kMaxR + 1];   // c_l / h^2
+    Source src;
+    RecLattice rec;
+    DevState *st;
+    unsigned int ncta;
+};
+
+// Launch configuration of one sweep.
+struct Launch {
+    int tx, ty;             // tile (x multiple of 4)
+    int zchunk;             // planes per CTA
+    int lookahead;          // TMA planes in flight ahead of use
+};
+
+// Kernel launchers (iso_sweep.cu, vti_sweep.cu, aux_kernels.cu).  Return a cudaError_t.
+cudaError_t launch_iso(int R, const Launch &L, const CUtensorMap &tm_cur, const IsoArgs &a,
+                       cudaStream_t s);
+cudaError_t launch_vti(int rxy, int rz, const Launch &L, const CUtensorMap &tm_p, const VtiArgs &a,
+                       cudaStream_t s);
+bool iso_supported(int R);
+bool iso_config_built(int R, const Launch &L);
+bool vti_config_built(int rxy, int rz, const Launch &L);
+bool vti_supported(int rxy, int rz);
+int iso_smem_bytes(int R, const Launch &L);
+int vti_smem_bytes(int rxy, const Launch &L);
+
+cudaError_t launch_model_iso(const float *v, long long src_pitch, float *kappa, int nx, int ny,
+                             int nz, long long pitch, double dt, DevState *st, cudaStream_t s);
+cudaError_t launch_model_vti(const float *vz, const float *eps, const float *delta,
+                             long long src_pitch, float *kx, float *kn, float *kz, int nx, int ny,
+                             int nz, long long pitch, double dt, DevState *st, cudaStream_t s);
+cudaError_t launch_gather(const float *field, long long pitch, long long plane, const int *idx,
+                          int nrec, float *trace, int t0, int cap, const DevState *st,
+                          cudaStream_t s);
+
+}  // namespace fdk

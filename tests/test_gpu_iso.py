@@ -1,0 +1,205 @@
+"""Isotropic sweep on the GPU against the FP64 oracle, through the C ABI.
+
+Tolerance (FP32 arithmetic with FP32 accumulation against FP64): one step
+rounds each point to ~1e-7 of the field's scale (the kappa-weighted stencil sum
+is small next to 2u - u_prev), and the error grows at most linearly with the
+step count, so after 200 steps the field error stays within ~2.4e-5 of the
+field maximum.  The tests use max |gpu - oracle| <= 1e-4 * max |oracle| per
+element and relative L2 <= 1e-4 (the target on the 64^3 case); one step from
+identical FP32 state is held to 2e-6 of the field maximum.
+"""
+import numpy as np
+import pytest
+
+from paper_1410_1387_gb300 import synth
+from tests.helpers import iso_shot, max_rel, oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1410_1387_gb300 import fd as fdmod
+    return fdmod
+
+
+def _run_gpu(fd, shot, nsteps, **kw):
+    g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=nsteps)
+    for k, v in kw.items():
+        getattr(g, k)(*v)
+    g.run(nsteps)
+    st = g.state()
+    tr = g.traces() if g.nrec else None
+    g.close()
+    return st, tr
+
+
+def test_parity_64_radius4_200_steps(fd, O):
+    shot = synth.parity_shot_64()
+    (u, up), tr = _run_gpu(fd, shot, 200)
+    P = oracle_problem(O, shot)
+    ur, upr, trr = P.iso_run(shot.v, 200)
+    assert rel_l2(u, ur) <= 1e-4
+    assert max_rel(u, ur) <= 1e-4
+    assert rel_l2(tr, trr) <= 1e-4
+    assert np.abs(ur).max() > 0 and np.isfinite(u).all()
+
+
+@pytest.mark.parametrize("R,shape,nb,steps", [
+    (4, (70, 45, 37), 6, 60),        # ragged x (not a multiple of 4), several tiles, sponge
+    (4, (131, 17, 90), 9, 40),       # more z chunks than one, ragged tile in y
+    (8, (66, 50, 41), 7, 60),
+    (8, (29, 33, 19), 0, 30),
+])
+def test_parity_ragged(fd, O, R, shape, nb, steps):
+    nx, ny, nz = shape
+    rec = synth.receiver_plane(nx, ny, nz // 3, stride=2, x0=1, y0=2)
+    shot = iso_shot(nx, ny, nz, R, steps, seed=7 + R, nb=nb, src=(nx // 3, ny // 2, nz // 2),
+                    receivers=rec)
+    (u, up), tr = _run_gpu(fd, shot, steps)
+    P = oracle_problem(O, shot)
+    ur, upr, trr = P.iso_run(shot.v, steps)
+    assert max_rel(u, ur) <= 1e-4
+    assert rel_l2(u, ur) <= 1e-4
+    # stored older level: the oracle keeps G * (what the sweep stores)
+    assert max_rel(P.sponge_field() * up, upr) <= 1e-4
+    assert max_rel(tr, trr) <= 1e-4
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 1), (5, 7, 3), (4, 4, 9), (9, 1, 12)])
+@pytest.mark.parametrize("R", [4, 8])
+def test_parity_degenerate_grids(fd, O, R, shape):
+    nx, ny, nz = shape
+    shot = iso_shot(nx, ny, nz, R, 12, seed=3, nb=0, src=(nx // 2, ny // 2, nz // 2),
+                    receivers=np.array([[nx - 1, ny - 1, nz - 1], [0, 0, 0]], np.int32),
+                    layered=False)
+    (u, up), tr = _run_gpu(fd, shot, 12)
+    P = oracle_problem(O, shot)
+    ur, upr, trr = P.iso_run(shot.v, 12)
+    assert max_rel(u, ur) <= 1e-4
+    assert max_rel(tr, trr) <= 1e-4
+
+
+def test_anisotropic_spacing(fd, O):
+    shot = iso_shot(40, 36, 33, 4, 50, seed=11, nb=4, dz=7.0)
+    (u, up), _ = _run_gpu(fd, shot, 50)
+    ur, _, _ = oracle_problem(O, shot).iso_run(shot.v, 50)
+    assert max_rel(u, ur) <= 1e-4
+
+
+def test_receivers_gather_matches_lattice(fd, O):
+    shot = iso_shot(48, 40, 30, 4, 30, seed=5, nb=5)
+    lattice = synth.receiver_plane(48, 40, 12, stride=3, x0=2, y0=1)
+    rng = np.random.default_rng(0)
+    scattered = np.stack([rng.integers(0, 48, 50), rng.integers(0, 40, 50), rng.integers(0, 30, 50)],
+                         axis=1).astype(np.int32)
+    shot.receivers = lattice
+    _, tr_lat = _run_gpu(fd, shot, 30)
+    shot.receivers = scattered
+    (u, _), tr_sc = _run_gpu(fd, shot, 30)
+    shot.receivers = lattice
+    _, _, trr = oracle_problem(O, shot).iso_run(shot.v, 30)
+    assert max_rel(tr_lat, trr) <= 1e-4
+    shot.receivers = scattered
+    _, _, trs = oracle_problem(O, shot).iso_run(shot.v, 30)
+    assert max_rel(tr_sc, trs) <= 1e-4
+
+
+def test_graph_and_tiles_are_bitwise_identical(fd):
+    shot = iso_shot(100, 70, 60, 4, 24, seed=9, nb=8)
+    (u0, p0), t0 = _run_gpu(fd, shot, 24)
+    (u1, p1), t1 = _run_gpu(fd, shot, 24, set_graph=(8,))
+    (u2, p2), t2 = _run_gpu(fd, shot, 24, set_launch=(64, 8, 13, 2))
+    (u3, p3), t3 = _run_gpu(fd, shot, 24, set_launch=(128, 8, 60, 2))
+    for a, b in ((u0, u1), (u0, u2), (u0, u3), (p0, p1), (p0, p3)):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(t0, t2)
+
+
+def test_checkpoint_resume_is_bitwise(fd):
+    shot = iso_shot(60, 50, 40, 4, 40, seed=13, nb=6)
+    (u_full, p_full), tr_full = _run_gpu(fd, shot, 40)
+    g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=40)
+    g.run(17)
+    cur, prev = g.state()
+    n = g.time_index
+    g.close()
+    g2 = fd.grid_from_shot(shot, device="cuda:0", nt_cap=40)
+    fd.fd_set_state(g2.h, cur, prev, ptr_kind=fd.FD_PTR_HOST, time_index=n)
+    g2.set_receivers(shot.receivers, 40) if shot.receivers is not None else None
+    g2.run(23)
+    u2, p2 = g2.state()
+    g2.close()
+    np.testing.assert_array_equal(u2, u_full)
+    np.testing.assert_array_equal(p2, p_full)
+
+
+def test_error_codes(fd):
+    import torch
+    shot = iso_shot(20, 20, 20, 4, 5, seed=1)
+    g = fd.Grid(fd.GridSpec.from_shot(shot), device="cuda:0")
+    with pytest.raises(fd.FdError) as e:
+        g.run(1)
+    assert e.value.code == fd.FD_ERR_BAD_STATE
+    bad = shot.v.copy()
+    bad[3, 4, 5] = np.nan
+    with pytest.raises(fd.FdError) as e:
+        g.set_model(bad)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+    with pytest.raises(fd.FdError) as e:
+        g.set_model(shot.v * 2.5)       # 2.5x the velocity: dt above the bound
+    assert e.value.code == fd.FD_ERR_UNSTABLE_DT
+    g.set_model(torch.from_numpy(shot.v).cuda())
+    with pytest.raises(fd.FdError) as e:
+        g.add_source(20, 0, 0)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+    g.set_receivers([[1, 2, 3]], 3)
+    g.run(3)
+    with pytest.raises(fd.FdError) as e:
+        g.run(1)
+    assert e.value.code == fd.FD_ERR_OUT_OF_RANGE
+    with pytest.raises(fd.FdError) as e:
+        g.traces(0, 4)
+    assert e.value.code == fd.FD_ERR_OUT_OF_RANGE
+    with pytest.raises(fd.FdError) as e:
+        g.set_launch(48, 16, 8, 2)
+    assert e.value.code == fd.FD_ERR_UNSUPPORTED
+    g.run(0)
+    g.sync()
+    g.close()
+
+
+@pytest.mark.parametrize("R", [4, 8])
+def test_full_size_512_one_step_sampled(fd, O, R):
+    """The 512^3 layered shot in the benchmark's launch configuration: after 30
+    steps, one more GPU step is checked point by point against the oracle's step
+    from the same single-precision state."""
+    shot = synth.layered_shot(512, R, nsteps=40)
+    g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=40)
+    g.run(30)
+    cur, prev = g.state()
+    g.step()
+    new, _ = g.state()
+    tr = g.traces(30, 1)[0]
+    g.close()
+    P = oracle_problem(O, shot, receivers=False)
+    rng = np.random.default_rng(R)
+    sx, sy, sz = shot.src
+    pts = [rng.integers(0, 512, size=(3000, 3))]
+    pts.append(np.array([[sx + a, sy + b, sz + c] for a in range(-5, 6) for b in (-3, 0, 3) for c in (-4, 0, 4)]))
+    pts.append(np.array([[i, j, k] for i in (0, 1, 19, 20, 255, 491, 492, 510, 511)
+                         for j in (0, 20, 300, 511) for k in (0, 3, 20, 21, 511)]))
+    pts = np.concatenate(pts).astype(np.int32)
+    sel = (pts[:, 2], pts[:, 1], pts[:, 0])
+    G = np.array([P.sponge_at(int(i), int(j), int(k)) for i, j, k in pts])
+    want = P.iso_step_points(shot.v, cur, pts, G * prev[sel].astype(np.float64), 30)
+    scale = np.abs(new).max()
+    assert scale > 0
+    assert np.abs(new[sel] - want).max() <= 2e-6 * scale
+    # the receiver plane row of this step is the new level at k = 20
+    np.testing.assert_array_equal(tr.reshape(512, 512), new[shot.nb])
