@@ -218,6 +218,34 @@ int fd_destroy_grid(fd_grid_t *g);
 /* Copy the calling thread's last error message into buf (always terminated). */
 int fd_last_error(char *buf, size_t n);
 
+/*
+ * One isotropic step that allocates no device memory.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc -- a serving
+ * process whose own pool allocator owns all device memory, or a
+ * latency-critical loop that cannot take the device-wide synchronisation that
+ * cudaMalloc / cudaFree may cause -- and so cannot use fd_create_grid().
+ *
+ * Same arithmetic and kernel as fd_step() on an isotropic grid: u_prev holds
+ * the stored older level on entry and u^{n+1} on return (in place), u_cur is
+ * u^n, kappa = (v dt)^2; all three are device arrays in the pitched layout of
+ * fd_layout(d) (16-byte aligned), owned by the caller.  n is the time index of
+ * u_cur and selects the Ricker sample s(n dt - t0) of the source at (src_ix,
+ * src_iy, src_iz); src_ix < 0 means no source.  No receivers.  Asynchronous
+ * on `stream`.
+ *
+ * Its scratch (status block, damping profiles, source sample) lives in a
+ * fixed __device__ array of about 97 KiB that every GPU loading the library
+ * holds until exit.  Grids with an axis above FD_STATIC_MAX_AXIS points are
+ * rejected with FD_ERR_OUT_OF_RANGE.  Every call rewrites that array on its
+ * stream, so calls that may overlap on the GPU (different streams or host
+ * threads without ordering) race; the first call on a device looks up the
+ * array's address and should come before any stream capture on that device.
+ */
+#define FD_STATIC_MAX_AXIS 8192
+int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u_prev, const float *kappa,
+                       int n, int src_ix, int src_iy, int src_iz, double freq_hz, double t0,
+                       double amp, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

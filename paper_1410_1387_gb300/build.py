@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfd.so")
 
-SOURCES = ["fd_api.cpp", "coeffs.cpp", "iso_sweep.cu", "vti_sweep.cu", "aux_kernels.cu"]
+SOURCES = ["fd_api.cpp", "coeffs.cpp", "iso_sweep.cu", "vti_sweep.cu", "aux_kernels.cu",
+           "fd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -322,6 +322,11 @@ int set_source_table(fd_grid *g, int ix, int iy, int iz, const std::vector<doubl
 
 }  // namespace
 
+namespace fdk {
+// Lets other translation units of the library report through fd_last_error().
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace fdk
+
 extern "C" {
 
 int fd_last_error(char *buf, size_t n)

@@ -37,6 +37,7 @@ EXPORTS = [
     "fd_add_source", "fd_add_source_series", "fd_set_receivers", "fd_step", "fd_run",
     "fd_set_graph", "fd_read_receivers", "fd_get_state", "fd_set_state", "fd_field",
     "fd_set_launch", "fd_time_index", "fd_sync", "fd_destroy_grid", "fd_last_error",
+    "fd_iso_step_static",
 ]
 
 
@@ -100,6 +101,7 @@ def lib() -> ctypes.CDLL:
             "fd_sync": [_vp],
             "fd_destroy_grid": [_vp],
             "fd_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+            "fd_iso_step_static": [D, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _d, _vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -239,6 +241,15 @@ def fd_sync(g) -> None:
 
 def fd_destroy_grid(g) -> None:
     _check(lib().fd_destroy_grid(g))
+
+
+def fd_iso_step_static(d: fd_desc, u_cur, u_prev, kappa, n, src=None, freq_hz=15.0, t0=None,
+                       amp=1.0, stream=0) -> None:
+    """One isotropic step with no device allocation (see include/fd.h)."""
+    sx, sy, sz = (-1, -1, -1) if src is None else src
+    t0 = 1.0 / freq_hz if t0 is None else t0
+    _check(lib().fd_iso_step_static(ctypes.byref(d), _ptr(u_cur), _ptr(u_prev), _ptr(kappa), n,
+                                    sx, sy, sz, freq_hz, t0, amp, stream))
 
 
 # ---- one shot on the GPU ---------------------------------------------------------
