@@ -46,21 +46,6 @@ int cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-int get_encode()
-{
-    if (g_encode) return FD_OK;
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                     cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-        return fail(FD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    return FD_OK;
-}
-
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 int check_desc(const fd_desc *d)
@@ -104,18 +89,8 @@ void compute_layout(const fd_desc *d, fd_layout_t *L)
 
 Launch default_launch(const fd_desc *d)
 {
-    Launch L;
-    L.tx = 64;
-    L.ty = 16;
-    L.lookahead = 2;
-    // z chunks: enough CTAs for several waves over 152 SMs x 2 resident CTAs
-    const long tiles = (long)((d->nx + L.tx - 1) / L.tx) * ((d->ny + L.ty - 1) / L.ty);
-    const long want = 152L * 2 * 4;
-    long chunks = std::max(1L, (want + tiles - 1) / tiles);
-    int zc = (int)((d->nz + chunks - 1) / chunks);
-    zc = std::max(zc, std::min(d->nz, 32));
-    L.zchunk = zc;
-    return L;
+    return d->mode == FD_MODE_ISO ? iso_default_launch(d->r_xy, d->nx, d->ny, d->nz)
+                                  : vti_default_launch(d->r_xy, d->r_z, d->nx, d->ny, d->nz);
 }
 
 }  // namespace
@@ -150,7 +125,9 @@ struct fd_grid {
     int *rec_idx = nullptr;
     // launch
     Launch L{};
-    CUtensorMap tm[2];
+    CUtensorMap tm_halo[2];      // u (p) buffers, box (tx + 2 r_xy) x (ty + 2 r_xy)
+    CUtensorMap tm_tile[4];      // every wavefield buffer, box tx x ty
+    CUtensorMap tm_model[3];     // every model buffer, box tx x ty
     // graphs
     int graph_steps = 0;
     cudaStream_t cap_stream = nullptr;
@@ -170,20 +147,17 @@ void drop_graphs(fd_grid *g)
 
 int make_tensor_maps(fd_grid *g)
 {
-    int rc = get_encode();
-    if (rc) return rc;
     const fd_desc &d = g->d;
-    const int R = d.r_xy;
-    cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
-    cuuint64_t strides[2] = {(cuuint64_t)g->lay.pitch * 4, (cuuint64_t)g->lay.pitch * d.ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)(g->L.tx + 2 * R), (cuuint32_t)(g->L.ty + 2 * R), 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    for (int b = 0; b < 2; ++b) {
-        CUresult r = g_encode(&g->tm[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, g->field[b], dims, strides,
-                              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    }
+    const int R = d.r_xy, tx = g->L.tx, ty = g->L.ty;
+    const long long pitch = g->lay.pitch;
+    int r = 0;
+    for (int b = 0; b < 2 && !r; ++b)
+        r = encode_field_map(&g->tm_halo[b], g->field[b], d.nx, d.ny, d.nz, pitch, tx + 2 * R, ty + 2 * R);
+    for (int b = 0; b < g->lay.nfields && !r; ++b)
+        r = encode_field_map(&g->tm_tile[b], g->field[b], d.nx, d.ny, d.nz, pitch, tx, ty);
+    for (int m = 0; m < g->lay.nmodel && !r; ++m)
+        r = encode_field_map(&g->tm_model[m], g->model[m], d.nx, d.ny, d.nz, pitch, tx, ty);
+    if (r) return fail(FD_ERR_CUDA, "tensor map encoding failed (%d)", r);
     return FD_OK;
 }
 
@@ -226,7 +200,8 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
         std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
         std::memcpy(a.wz, g->wz, sizeof a.wz);
         a.src = src; a.rec = rec; a.st = g->st;
-        e = launch_iso(d.r_xy, g->L, g->tm[cur], a, s);
+        const IsoMaps maps{g->tm_halo[cur], g->tm_tile[1 - cur], g->tm_model[0]};
+        e = launch_iso(d.r_xy, g->L, maps, a, s);
         newbuf = a.prev;
     } else {
         VtiArgs a{};
@@ -243,7 +218,9 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
         a.w0 = g->w0;
         std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
         a.src = src; a.rec = rec; a.st = g->st;
-        e = launch_vti(d.r_xy, d.r_z, g->L, g->tm[cur], a, s);
+        const VtiMaps maps{g->tm_halo[cur],    g->tm_tile[2 + cur], g->tm_tile[1 - cur], g->tm_tile[3 - cur],
+                           g->tm_model[0],     g->tm_model[1],      g->tm_model[2]};
+        e = launch_vti(d.r_xy, d.r_z, g->L, maps, a, s);
         newbuf = a.pprev;
     }
     if (e != cudaSuccess) return e;

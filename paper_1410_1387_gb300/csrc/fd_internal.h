@@ -85,17 +85,42 @@ struct Launch {
     int lookahead;          // TMA planes in flight ahead of use
 };
 
+// Planes per CTA: enough CTAs (about 2048) for several waves over 152 SMs, at
+// least 32 planes per chunk so that the queue priming stays a small share.
+inline int default_zchunk(const Launch &L, int nx, int ny, int nz)
+{
+    const long tiles = (long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
+    long chunks = (2048 + tiles - 1) / tiles;
+    if (chunks < 1) chunks = 1;
+    int zc = (int)((nz + chunks - 1) / chunks);
+    const int lo = nz < 32 ? nz : 32;
+    return zc < lo ? lo : zc;
+}
+
+// Tensor maps of one isotropic launch: u^n with the R halo, u^{n-1} and kappa tiles.
+struct IsoMaps {
+    CUtensorMap cur, prev, kappa;
+};
+
+// 3D tensor map over a pitched nx x ny x nz float field, box (bx, by, 1).
+// Returns 0 or a CUresult / cudaError_t code.
+int encode_field_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, long long pitch, int bx,
+                     int by);
+
 // Kernel launchers (iso_sweep.cu, vti_sweep.cu, aux_kernels.cu).  Return a cudaError_t.
-cudaError_t launch_iso(int R, const Launch &L, const CUtensorMap &tm_cur, const IsoArgs &a,
-                       cudaStream_t s);
-cudaError_t launch_vti(int rxy, int rz, const Launch &L, const CUtensorMap &tm_p, const VtiArgs &a,
-                       cudaStream_t s);
+cudaError_t launch_iso(int R, const Launch &L, const IsoMaps &tm, const IsoArgs &a, cudaStream_t s);
+// Tensor maps of one VTI launch: p^n with the R_xy halo, tiles of q^n, p_prev,
+// q_prev and the three kappa arrays.
+struct VtiMaps {
+    CUtensorMap p, q, pp, qp, kx, kn, kz;
+};
+cudaError_t launch_vti(int rxy, int rz, const Launch &L, const VtiMaps &tm, const VtiArgs &a, cudaStream_t s);
+Launch iso_default_launch(int R, int nx, int ny, int nz);
+Launch vti_default_launch(int rxy, int rz, int nx, int ny, int nz);
 bool iso_supported(int R);
 bool iso_config_built(int R, const Launch &L);
 bool vti_config_built(int rxy, int rz, const Launch &L);
 bool vti_supported(int rxy, int rz);
-int iso_smem_bytes(int R, const Launch &L);
-int vti_smem_bytes(int rxy, const Launch &L);
 
 cudaError_t launch_model_iso(const float *v, long long src_pitch, float *kappa, int nx, int ny,
                              int nz, long long pitch, double dt, DevState *st, cudaStream_t s);

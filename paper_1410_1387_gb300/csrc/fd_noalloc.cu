@@ -68,20 +68,6 @@ struct HostTables {
 };
 thread_local HostTables t_tables;
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
 int err(int code, const char *msg) { return set_last_error(code, msg); }
 
 int cuda_err(cudaError_t e, const char *what)
@@ -119,8 +105,6 @@ extern "C" int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u
         return err(FD_ERR_INVALID_ARG, "source cell outside the grid");
     if (has_src && (!(freq_hz > 0.0) || !std::isfinite(freq_hz) || !std::isfinite(t0) || !std::isfinite(amp)))
         return err(FD_ERR_INVALID_ARG, "bad Ricker parameters");
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-    if (!enc) return err(FD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -159,23 +143,12 @@ extern "C" int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u
         if (e != cudaSuccess) return cuda_err(e, "scratch upload");
     }
 
-    Launch L;
-    L.tx = 64;
-    L.ty = 16;
-    L.lookahead = 2;
-    const long tiles = (long)((d->nx + L.tx - 1) / L.tx) * ((d->ny + L.ty - 1) / L.ty);
-    const long chunks = std::max(1L, (152L * 2 * 4 + tiles - 1) / tiles);
-    L.zchunk = std::max((int)((d->nz + chunks - 1) / chunks), std::min(d->nz, 32));
-
-    CUtensorMap tm;
-    cuuint64_t dims[3] = {(cuuint64_t)d->nx, (cuuint64_t)d->ny, (cuuint64_t)d->nz};
-    cuuint64_t strides[2] = {(cuuint64_t)lay.pitch * 4, (cuuint64_t)lay.pitch * d->ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)(L.tx + 2 * R), (cuuint32_t)(L.ty + 2 * R), 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult cr = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(u_cur), dims, strides, box, es,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return err(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    const Launch L = iso_default_launch(R, d->nx, d->ny, d->nz);
+    IsoMaps tm;
+    int cr = encode_field_map(&tm.cur, u_cur, d->nx, d->ny, d->nz, lay.pitch, L.tx + 2 * R, L.ty + 2 * R);
+    if (!cr) cr = encode_field_map(&tm.prev, u_prev, d->nx, d->ny, d->nz, lay.pitch, L.tx, L.ty);
+    if (!cr) cr = encode_field_map(&tm.kappa, kappa, d->nx, d->ny, d->nz, lay.pitch, L.tx, L.ty);
+    if (cr) return err(FD_ERR_CUDA, "tensor map encoding failed");
 
     IsoArgs a{};
     a.prev = u_prev;

@@ -38,6 +38,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// Plain arrival (release semantics at CTA scope): this thread's earlier shared
+// memory reads of the slot are ordered before the producer's next overwrite.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // One non-blocking probe of phase `parity`; true once that phase completed.
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 {

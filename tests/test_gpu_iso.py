@@ -114,8 +114,8 @@ def test_graph_and_tiles_are_bitwise_identical(fd):
     shot = iso_shot(100, 70, 60, 4, 24, seed=9, nb=8)
     (u0, p0), t0 = _run_gpu(fd, shot, 24)
     (u1, p1), t1 = _run_gpu(fd, shot, 24, set_graph=(8,))
-    (u2, p2), t2 = _run_gpu(fd, shot, 24, set_launch=(64, 8, 13, 2))
-    (u3, p3), t3 = _run_gpu(fd, shot, 24, set_launch=(128, 8, 60, 2))
+    (u2, p2), t2 = _run_gpu(fd, shot, 24, set_launch=(64, 8, 13, 3))
+    (u3, p3), t3 = _run_gpu(fd, shot, 24, set_launch=(128, 8, 60, 3))
     for a, b in ((u0, u1), (u0, u2), (u0, u3), (p0, p1), (p0, p3)):
         np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(t0, t2)
