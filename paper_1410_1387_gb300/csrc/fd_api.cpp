@@ -163,8 +163,8 @@ int make_tensor_maps(fd_grid *g)
 
 int set_launch(fd_grid *g, const Launch &L)
 {
-    if (L.tx <= 0 || L.ty <= 0 || L.zchunk <= 0 || L.lookahead <= 0)
-        return fail(FD_ERR_INVALID_ARG, "bad launch configuration");
+    if (L.tx <= 0 || L.ty <= 0 || L.zchunk <= 0 || L.lookahead <= 0 || L.zchunk > kMaxChunk)
+        return fail(FD_ERR_INVALID_ARG, "bad launch configuration (z chunk 1..%d)", kMaxChunk);
     if ((g->d.ny + L.ty - 1) / L.ty > 65535 || (g->d.nz + L.zchunk - 1) / L.zchunk > 65535)
         return fail(FD_ERR_INVALID_ARG, "launch grid too large");
     const bool built = g->d.mode == FD_MODE_ISO ? iso_config_built(g->d.r_xy, L)

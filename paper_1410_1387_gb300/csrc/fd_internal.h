@@ -85,16 +85,21 @@ struct Launch {
     int lookahead;          // TMA planes in flight ahead of use
 };
 
+// Largest z chunk of one CTA (its damping factors are staged in shared memory).
+constexpr int kMaxChunk = 1024;
+
 // Planes per CTA: enough CTAs (about 2048) for several waves over 152 SMs, at
-// least 32 planes per chunk so that the queue priming stays a small share.
+// least 16 planes per chunk (small grids) so that priming the z queue stays a
+// small share, and at most kMaxChunk.
 inline int default_zchunk(const Launch &L, int nx, int ny, int nz)
 {
     const long tiles = (long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
     long chunks = (2048 + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
     int zc = (int)((nz + chunks - 1) / chunks);
-    const int lo = nz < 32 ? nz : 32;
-    return zc < lo ? lo : zc;
+    const int lo = nz < 16 ? nz : 16;
+    zc = zc < lo ? lo : zc;
+    return zc > kMaxChunk ? kMaxChunk : zc;
 }
 
 // Tensor maps of one isotropic launch: u^n with the R halo, u^{n-1} and kappa tiles.

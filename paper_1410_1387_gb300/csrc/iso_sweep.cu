@@ -45,7 +45,9 @@ struct IsoCfg {
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
-    static constexpr int SMEM = OFF_BAR + 8 * (2 * NA + 2 * NB) + 16;
+    static constexpr int OFF_GZ = OFF_BAR + 8 * (2 * NA + 2 * NB) + 16;
+    // + 4 bytes per plane of the chunk (damping factors along z), added at launch
+    static constexpr int SMEM = OFF_GZ;
     static_assert(TX % 4 == 0 && R % 4 == 0, "x alignment");
     static_assert(NC % 32 == 0, "whole consumer warps");
     static_assert((SLOT_A * 4) % 128 == 0 && (SLOT_B * 4) % 128 == 0, "slot alignment");
@@ -97,6 +99,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
         sh[2] = z0;
         sh[3] = z0;
     }
+    float *sgz = reinterpret_cast<float *>(smem_raw + C::OFF_GZ);   // z damping factors of the chunk
+    for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
     __syncthreads();
     const int n = sh[0];
     bool failed = false;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             const float *tb = ringB + sb * C::SLOT_B;
             const float4 pv = *reinterpret_cast<const float4 *>(tb + ownb);
             const float4 kv = *reinterpret_cast<const float4 *>(tb + TX * TY + ownb);
-            const float gz = a.gz[k];
+            const float gz = sgz[k - z0];
 
             const int sa = (k - z0) % C::NA;
             const float *t = ringA + sa * C::SLOT_A;
@@ -326,33 +330,35 @@ template <int R, int TX, int TY, int LA>
 static cudaError_t launch_t(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s)
 {
     using C = IsoCfg<R, TX, TY, LA>;
+    constexpr int smem_max = C::SMEM + 4 * kMaxChunk;
     static bool attr_set[64] = {};   // per device
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(iso_sweep_kernel<R, TX, TY, LA>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     IsoArgs a = a0;
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
-    iso_sweep_kernel<R, TX, TY, LA><<<grid, C::NT, C::SMEM, s>>>(tm.cur, tm.prev, tm.kappa, a);
+    const int smem = C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4);
+    iso_sweep_kernel<R, TX, TY, LA><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, a);
     return cudaGetLastError();
 }
 
 // The (R, tile, lookahead) combinations built into the library.
 #define FD_ISO_CONFIGS(X) \
     X(4, 64, 16, 3)       \
+    X(4, 64, 16, 4)       \
     X(4, 64, 16, 2)       \
     X(4, 64, 8, 3)        \
     X(4, 128, 8, 3)       \
     X(4, 32, 16, 3)       \
     X(8, 64, 8, 2)        \
     X(8, 64, 8, 3)        \
-    X(8, 32, 16, 2)       \
-    X(8, 64, 16, 2)
+    X(8, 32, 16, 2)
 
 cudaError_t launch_iso(int R, const Launch &L, const IsoMaps &tm, const IsoArgs &a, cudaStream_t s)
 {
