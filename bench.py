@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="iso512_r4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="iso512_r4", choices=sorted(WORKLOADS) + ["survey64"])
     ap.add_argument("--n", type=int, default=512, help="grid points per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -371,12 +371,50 @@ def run_ours(args):
     return 0
 
 
+def run_survey(args):
+    """64 independent shots (cubic 96^3..320^3, 300..1500 steps, radius 4, own
+    layered models): one batch (autotuned tile and z chunk, CUDA graphs) vs the
+    plain loop of fd_run per shot, same traces required bit for bit."""
+    import torch
+
+    from paper_1410_1387_gb300 import batch, synth
+
+    torch.cuda.set_device(0)
+    shots = synth.survey_shots(64, seed=2024)
+    pts = sum(s.points * s.nsteps for s in shots)
+    tuner = batch.Autotuner()
+    choice = tuner.batch(shots[:16], steps=4)
+    tr_b, t_b, _, g_b = batch.run_batched(shots, graph_steps=16, launch=choice)
+    torch.cuda.empty_cache()
+    tr_s, t_s, _, g_s = batch.run_per_shot(shots)
+    same = batch.traces_equal(tr_b, tr_s)
+    trace_bytes = sum(4 * len(s.receivers) * s.nsteps for s in shots)
+    line = {
+        "metric": METRIC, "value": len(shots) / g_b, "unit": "shots/s", "n_gpus": 1, "steps": None,
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": "survey64_batched", "shots": len(shots),
+                   "grids": "cubic, n ~ U{96..320}", "steps": "U{300..1500}", "radius": 4,
+                   "launch": {str(k): list(v) for k, v in choice.items()}, "graph_steps": 16},
+        "batched": {"shots_per_s": len(shots) / g_b, "gpu_seconds": g_b, "points_per_s": pts / g_b,
+                    "e2e_seconds": t_b, "e2e_shots_per_s": len(shots) / t_b},
+        "per_shot_loop": {"shots_per_s": len(shots) / g_s, "gpu_seconds": g_s, "points_per_s": pts / g_s,
+                          "e2e_seconds": t_s, "e2e_shots_per_s": len(shots) / t_s},
+        "speedup_vs_loop": g_s / g_b, "e2e_speedup_vs_loop": t_s / t_b,
+        "trace_bytes_read_back": trace_bytes, "traces_identical": bool(same),
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "survey64":
+        return run_survey(args)
     return run_ours(args)
 
 

@@ -218,6 +218,49 @@ int fd_destroy_grid(fd_grid_t *g);
 /* Copy the calling thread's last error message into buf (always terminated). */
 int fd_last_error(char *buf, size_t n);
 
+/* ---- batched shots --------------------------------------------------------
+ * Many independent isotropic shots (radius 4 or 8, any sizes and step counts)
+ * advanced together: each launch performs one time step (Eq. 3, exactly the
+ * arithmetic of fd_step) of every member shot, its CTAs drawn from one work
+ * list of (shot, tile, z chunk) items, so that small grids share the GPU
+ * instead of each leaving most SMs idle.  Each member keeps its own buffers,
+ * model, source and receivers (a receiver set must be a lattice on one plane).
+ * A shot's own time index picks its current buffer on the device, so a CUDA
+ * graph of several batch launches replays without per-step arguments; members
+ * that have run their steps skip their items.  An extension of the paper's
+ * single-shot step for seismic surveys (many shots per model).
+ */
+typedef struct fd_batch fd_batch_t;
+
+/* New empty batch ordered on `stream` (the member grids' work must be ordered
+   before it by the caller, e.g. by using the same stream). */
+int fd_batch_create(void *stream, fd_batch_t **out);
+
+/* Tile (tx x ty, lookahead) and z chunk used for members of the given radius;
+   zchunk 0 = each member grid's own (fd_set_launch).  Defaults: radius 4:
+   64 x 16, 64 planes, lookahead 3; radius 8: 64 x 8, 64 planes, lookahead 2. */
+int fd_batch_set_launch(fd_batch_t *b, int radius, int tx, int ty, int zchunk, int lookahead);
+
+/* Replay CUDA graphs of `steps` batch launches in fd_batch_run (0 = plain launches). */
+int fd_batch_set_graph(fd_batch_t *b, int steps);
+
+/* Add grid g (isotropic, model set) to run `nsteps` more steps in the batch.
+   The grid stays owned by the caller and must outlive its membership. */
+int fd_batch_add(fd_batch_t *b, fd_grid_t *g, int nsteps);
+
+/* Detach g (finished, or cancelled between runs). */
+int fd_batch_remove(fd_batch_t *b, fd_grid_t *g);
+
+/* Steps g still has to run in the batch. */
+int fd_batch_steps_left(fd_batch_t *b, fd_grid_t *g, int *left);
+
+/* Up to max_steps batch launches, fewer when every member is done;
+   *steps_run (may be NULL) receives the number of launches. */
+int fd_batch_run(fd_batch_t *b, int max_steps, int *steps_run);
+
+/* Release the batch (not its member grids). */
+int fd_batch_destroy(fd_batch_t *b);
+
 /*
  * One isotropic step that allocates no device memory.  The paper has no
  * counterpart: this is for callers that cannot call cudaMalloc -- a serving

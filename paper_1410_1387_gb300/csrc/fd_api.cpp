@@ -178,6 +178,27 @@ int set_launch(fd_grid *g, const Launch &L)
 }
 
 // Enqueue one time step on stream s (no host-side bookkeeping).
+// Everything of an isotropic launch except the two buffer pointers.
+IsoArgs iso_args(const fd_grid *g)
+{
+    const fd_desc &d = g->d;
+    IsoArgs a{};
+    a.kappa = g->model[0];
+    a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
+    a.pitch = g->lay.pitch;
+    a.plane = (long long)g->lay.pitch * d.ny;
+    a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
+    a.zchunk = g->L.zchunk;
+    a.w0 = g->w0;
+    std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
+    std::memcpy(a.wz, g->wz, sizeof a.wz);
+    a.src = Source{g->src_tab, g->src_len, g->sx, g->sy, g->sz, g->into_q};
+    a.rec = g->lat;
+    a.rec.on = (g->nrec > 0 && g->lattice) ? 1 : 0;
+    a.st = g->st;
+    return a;
+}
+
 cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
 {
     const fd_desc &d = g->d;
@@ -188,18 +209,9 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
     cudaError_t e;
     float *newbuf;
     if (d.mode == FD_MODE_ISO) {
-        IsoArgs a{};
+        IsoArgs a = iso_args(g);
         a.prev = g->field[1 - cur];
         a.cur = g->field[cur];
-        a.kappa = g->model[0];
-        a.gx = g->gx; a.gy = g->gy; a.gz = g->gz;
-        a.pitch = pitch; a.plane = plane;
-        a.nx = d.nx; a.ny = d.ny; a.nz = d.nz;
-        a.zchunk = g->L.zchunk;
-        a.w0 = g->w0;
-        std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
-        std::memcpy(a.wz, g->wz, sizeof a.wz);
-        a.src = src; a.rec = rec; a.st = g->st;
         const IsoMaps maps{g->tm_halo[cur], g->tm_tile[1 - cur], g->tm_model[0]};
         e = launch_iso(d.r_xy, g->L, maps, a, s);
         newbuf = a.prev;
@@ -732,6 +744,271 @@ int fd_destroy_grid(fd_grid_t *g)
         if (p) cudaFree(p);
     if (g->st_host) cudaFreeHost(g->st_host);
     delete g;
+    cudaGetLastError();
+    return FD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched isotropic shots: one launch per time step over every member's tiles.
+
+struct fd_batch {
+    struct Member {
+        fd_grid *g;
+        int n_end;
+    };
+    cudaStream_t stream = nullptr;
+    std::vector<Member> members;
+    Launch L[2];                        // radius 4, radius 8 (zchunk 0 = each member's own)
+    BatchShot *d_shots = nullptr;
+    size_t cap_shots = 0;
+    int4 *d_items = nullptr;
+    size_t cap_items = 0;
+    int nitems[2] = {0, 0}, off[2] = {0, 0}, max_zc[2] = {1, 1};
+    bool dirty = true;
+    int graph_steps = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+int radius_slot(int R) { return R == 4 ? 0 : (R == 8 ? 1 : -1); }
+
+void batch_drop_graph(fd_batch *b)
+{
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+}
+
+int batch_rebuild(fd_batch *b)
+{
+    const size_t ns = b->members.size();
+    std::vector<BatchShot> shots(ns);
+    std::vector<int4> items[2];
+    for (int r = 0; r < 2; ++r) b->max_zc[r] = 1;
+    for (size_t i = 0; i < ns; ++i) {
+        fd_grid *g = b->members[i].g;
+        const fd_desc &d = g->d;
+        const int ri = radius_slot(d.r_xy), R = d.r_xy;
+        const Launch &L = b->L[ri];
+        BatchShot &s = shots[i];
+        std::memset(static_cast<void *>(&s), 0, sizeof s);
+        const long long pitch = g->lay.pitch;
+        int r = 0;
+        for (int k = 0; k < 2 && !r; ++k)
+            r = encode_field_map(&s.halo[k], g->field[k], d.nx, d.ny, d.nz, pitch, L.tx + 2 * R, L.ty + 2 * R);
+        for (int k = 0; k < 2 && !r; ++k)
+            r = encode_field_map(&s.tile[k], g->field[k], d.nx, d.ny, d.nz, pitch, L.tx, L.ty);
+        if (!r) r = encode_field_map(&s.kappa, g->model[0], d.nx, d.ny, d.nz, pitch, L.tx, L.ty);
+        if (r) return fail(FD_ERR_CUDA, "tensor map encoding failed (%d)", r);
+        s.a = iso_args(g);
+        const int zc = L.zchunk > 0 ? std::min(L.zchunk, d.nz) : g->L.zchunk;
+        s.a.zchunk = zc;
+        s.buf[0] = g->field[0];
+        s.buf[1] = g->field[1];
+        s.n0 = g->n;
+        s.cur0 = g->cur;
+        s.n_end = b->members[i].n_end;
+        const int gx = (d.nx + L.tx - 1) / L.tx, gy = (d.ny + L.ty - 1) / L.ty, gz = (d.nz + zc - 1) / zc;
+        s.ncta = (unsigned)gx * gy * gz;
+        s.a.ncta = s.ncta;
+        b->max_zc[ri] = std::max(b->max_zc[ri], zc);
+        for (int bz = 0; bz < gz; ++bz)
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) items[ri].push_back(make_int4((int)i, bx, by, bz));
+    }
+    const size_t nit = items[0].size() + items[1].size();
+    if (nit > 0x7fffffff) return fail(FD_ERR_OUT_OF_RANGE, "batch has too many work items");
+    if (ns > b->cap_shots) {
+        if (b->d_shots) cudaFree(b->d_shots);
+        b->d_shots = nullptr;
+        b->cap_shots = 0;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_shots), ns * sizeof(BatchShot));
+        if (e != cudaSuccess) return cuda_fail(e, "batch descriptor allocation");
+        b->cap_shots = ns;
+    }
+    if (nit > b->cap_items) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->cap_items = 0;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_items), std::max<size_t>(nit, 1) * sizeof(int4));
+        if (e != cudaSuccess) return cuda_fail(e, "batch work-list allocation");
+        b->cap_items = std::max<size_t>(nit, 1);
+    }
+    if (ns) CU(cudaMemcpyAsync(b->d_shots, shots.data(), ns * sizeof(BatchShot), cudaMemcpyHostToDevice, b->stream),
+               "batch descriptor upload");
+    b->off[0] = 0;
+    b->nitems[0] = (int)items[0].size();
+    b->off[1] = b->nitems[0];
+    b->nitems[1] = (int)items[1].size();
+    for (int r = 0; r < 2; ++r)
+        if (b->nitems[r])
+            CU(cudaMemcpyAsync(b->d_items + b->off[r], items[r].data(), items[r].size() * sizeof(int4),
+                               cudaMemcpyHostToDevice, b->stream),
+               "batch work-list upload");
+    CU(cudaStreamSynchronize(b->stream), "batch upload");
+    b->dirty = false;
+    batch_drop_graph(b);
+    return FD_OK;
+}
+
+cudaError_t batch_enqueue_step(fd_batch *b, cudaStream_t s)
+{
+    const int radii[2] = {4, 8};
+    for (int r = 0; r < 2; ++r) {
+        if (!b->nitems[r]) continue;
+        cudaError_t e = launch_iso_batch(radii[r], b->L[r], b->d_items + b->off[r], b->nitems[r], b->d_shots,
+                                         b->max_zc[r], s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fd_batch_create(void *stream, fd_batch_t **out)
+{
+    if (!out) return fail(FD_ERR_INVALID_ARG, "out is NULL");
+    fd_batch *b = new (std::nothrow) fd_batch;
+    if (!b) return fail(FD_ERR_NO_MEMORY, "host allocation failed");
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->L[0] = Launch{64, 16, 64, 3};
+    b->L[1] = Launch{64, 8, 64, 2};
+    *out = b;
+    return FD_OK;
+}
+
+int fd_batch_set_launch(fd_batch_t *b, int radius, int tx, int ty, int zchunk, int lookahead)
+{
+    if (!b) return fail(FD_ERR_INVALID_ARG, "batch is NULL");
+    const int ri = radius_slot(radius);
+    if (ri < 0) return fail(FD_ERR_UNSUPPORTED, "batches hold isotropic radius 4 or 8 shots");
+    if (zchunk < 0 || zchunk > kMaxChunk) return fail(FD_ERR_INVALID_ARG, "z chunk 0..%d", kMaxChunk);
+    Launch L{tx, ty, zchunk, lookahead};
+    if (!iso_config_built(radius, L))
+        return fail(FD_ERR_UNSUPPORTED, "tile %d x %d, lookahead %d is not built for radius %d", tx, ty, lookahead,
+                    radius);
+    b->L[ri] = L;
+    b->dirty = true;
+    return FD_OK;
+}
+
+int fd_batch_set_graph(fd_batch_t *b, int steps)
+{
+    if (!b) return fail(FD_ERR_INVALID_ARG, "batch is NULL");
+    if (steps < 0 || steps > 1024) return fail(FD_ERR_INVALID_ARG, "graph steps must be 0..1024");
+    batch_drop_graph(b);
+    b->graph_steps = steps;
+    return FD_OK;
+}
+
+int fd_batch_add(fd_batch_t *b, fd_grid_t *g, int nsteps)
+{
+    if (!b || !g) return fail(FD_ERR_INVALID_ARG, "NULL argument");
+    if (g->d.mode != FD_MODE_ISO || radius_slot(g->d.r_xy) < 0)
+        return fail(FD_ERR_UNSUPPORTED, "batches hold isotropic radius 4 or 8 shots");
+    if (!g->model_set) return fail(FD_ERR_BAD_STATE, "no model: call fd_set_model first");
+    if (nsteps < 0 || (long long)g->n + nsteps > 0x7fffffffLL) return fail(FD_ERR_INVALID_ARG, "bad step count");
+    if (g->nrec > 0 && !g->lattice)
+        return fail(FD_ERR_UNSUPPORTED, "batched shots need receivers on a lattice of one plane");
+    if (g->nrec > 0 && (long long)g->n + nsteps - g->rec_t0 > g->rec_cap)
+        return fail(FD_ERR_OUT_OF_RANGE, "receiver buffer too small for %d more steps", nsteps);
+    for (const auto &m : b->members)
+        if (m.g == g) return fail(FD_ERR_INVALID_ARG, "grid is already in the batch");
+    b->members.push_back({g, g->n + nsteps});
+    b->dirty = true;
+    return FD_OK;
+}
+
+int fd_batch_remove(fd_batch_t *b, fd_grid_t *g)
+{
+    if (!b || !g) return fail(FD_ERR_INVALID_ARG, "NULL argument");
+    for (size_t i = 0; i < b->members.size(); ++i)
+        if (b->members[i].g == g) {
+            b->members.erase(b->members.begin() + i);
+            b->dirty = true;
+            return FD_OK;
+        }
+    return fail(FD_ERR_INVALID_ARG, "grid is not in the batch");
+}
+
+int fd_batch_steps_left(fd_batch_t *b, fd_grid_t *g, int *left)
+{
+    if (!b || !g || !left) return fail(FD_ERR_INVALID_ARG, "NULL argument");
+    for (const auto &m : b->members)
+        if (m.g == g) {
+            *left = std::max(0, m.n_end - g->n);
+            return FD_OK;
+        }
+    return fail(FD_ERR_INVALID_ARG, "grid is not in the batch");
+}
+
+int fd_batch_run(fd_batch_t *b, int max_steps, int *steps_run)
+{
+    if (!b) return fail(FD_ERR_INVALID_ARG, "batch is NULL");
+    if (max_steps < 0) return fail(FD_ERR_INVALID_ARG, "negative step count");
+    if (steps_run) *steps_run = 0;
+    int need = 0;
+    for (const auto &m : b->members) need = std::max(need, m.n_end - m.g->n);
+    const int steps = std::min(max_steps, need);
+    if (steps == 0) return FD_OK;
+    if (b->dirty) {
+        int rc = batch_rebuild(b);
+        if (rc) return rc;
+    }
+    int left = steps;
+    const int K = b->graph_steps;
+    while (K > 0 && left >= K) {
+        if (!b->gexec) {
+            if (!b->cap_stream) CU(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream create");
+            CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t e = cudaSuccess;
+            for (int j = 0; j < K && e == cudaSuccess; ++j) e = batch_enqueue_step(b, b->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(e, "batch capture");
+            }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b->gexec = nullptr;
+                return cuda_fail(e, "graph instantiate");
+            }
+        }
+        CU(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
+        left -= K;
+    }
+    for (; left > 0; --left) {
+        cudaError_t e = batch_enqueue_step(b, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    }
+    for (auto &m : b->members) {
+        const int adv = std::max(0, std::min(steps, m.n_end - m.g->n));
+        m.g->n += adv;
+        m.g->cur ^= (adv & 1);
+    }
+    if (steps_run) *steps_run = steps;
+    return FD_OK;
+}
+
+int fd_batch_destroy(fd_batch_t *b)
+{
+    if (!b) return FD_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_shots) cudaFree(b->d_shots);
+    if (b->d_items) cudaFree(b->d_items);
+    delete b;
     cudaGetLastError();
     return FD_OK;
 }

@@ -42,7 +42,7 @@ struct Source {
 };
 
 // Arguments of the isotropic sweep (Eq. 3 with the Laplacian of Eq. 4 on all axes).
-struct IsoArgs {
+struct alignas(16) IsoArgs {
     float *prev;            // stored older level in, u^{n+1} out (in place)
     const float *cur;       // u^n (plain loads for the first planes of a z chunk)
     const float *kappa;     // (v dt)^2
@@ -114,6 +114,21 @@ int encode_field_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, 
 
 // Kernel launchers (iso_sweep.cu, vti_sweep.cu, aux_kernels.cu).  Return a cudaError_t.
 cudaError_t launch_iso(int R, const Launch &L, const IsoMaps &tm, const IsoArgs &a, cudaStream_t s);
+// One member shot of a batched isotropic launch (device array, one per shot).
+// The shot's time index n (its status block) picks the buffer holding u^n:
+// buf[cur0 ^ ((n - n0) & 1)]; launches stop advancing it once n reaches n_end.
+struct alignas(128) BatchShot {
+    CUtensorMap halo[2];    // u buffers with the R halo (box tile + 2R)
+    CUtensorMap tile[2];    // u buffers, box tile
+    CUtensorMap kappa;      // box tile
+    IsoArgs a;              // a.prev / a.cur unused
+    float *buf[2];
+    int n0, cur0, n_end;
+    unsigned ncta;          // CTAs of this shot per launch
+};
+cudaError_t launch_iso_batch(int R, const Launch &L, const int4 *items, int nitems, const BatchShot *shots,
+                             int max_zchunk, cudaStream_t s);
+
 // Tensor maps of one VTI launch: p^n with the R_xy halo, tiles of q^n, p_prev,
 // q_prev and the three kappa arrays.
 struct VtiMaps {

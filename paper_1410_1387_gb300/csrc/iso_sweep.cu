@@ -54,10 +54,35 @@ struct IsoCfg {
     static_assert(SW <= 256 && SH <= 256, "TMA box limit");
 };
 
+// The time index n of a shot: thread 0 reads it and counts this CTA; the last
+// of the shot's ncta CTAs advances it (so graph replays need no per-step
+// arguments).  Returns -1 to every thread when n >= n_end (a finished shot in a
+// batch: its CTAs do nothing).
+__device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_end, int *sh_n)
+{
+    if (threadIdx.x == 0) {
+        int n = *reinterpret_cast<volatile int *>(&st->step);
+        if (n >= n_end) {
+            n = -1;
+        } else {
+            __threadfence();
+            if (atomicAdd(&st->done, 1u) == ncta - 1) {
+                st->done = 0;
+                *reinterpret_cast<volatile int *>(&st->step) = n + 1;
+                __threadfence();
+            }
+        }
+        *sh_n = n;
+    }
+    __syncthreads();
+    return *sh_n;
+}
+
+// One CTA's work: tile (bx, by), z chunk bz, of the step u^n -> u^{n+1}.
 template <int R, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
-    iso_sweep_kernel(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
-                     const __grid_constant__ CUtensorMap tm_kappa, const IsoArgs a)
+__device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtensorMap *tm_prev,
+                                         const CUtensorMap *tm_kappa, const IsoArgs &a, float *prev,
+                                         const float *cur, const int n, const int bx, const int by, const int bz)
 {
     using C = IsoCfg<R, TX, TY, LA>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -71,8 +96,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     volatile int *sh_abort = sh + 1;
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zchunk;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int z0 = bz * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.nz);
     const int zend = min(z1 + R, a.nz);             // ring A planes: [z0, zend)
 
@@ -86,14 +111,6 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             mbar_init(&emptyB[s], C::NCW);
         }
         fence_mbar_init();
-        // Time index of u^n: every CTA reads it, the last CTA to do so advances it.
-        const int n = *reinterpret_cast<volatile int *>(&a.st->step);
-        __threadfence();
-        if (atomicAdd(&a.st->done, 1u) == a.ncta - 1) {
-            a.st->done = 0;
-            *reinterpret_cast<volatile int *>(&a.st->step) = n + 1;
-            __threadfence();
-        }
         sh[0] = n;
         sh[1] = 0;
         sh[2] = z0;
@@ -102,15 +119,14 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     float *sgz = reinterpret_cast<float *>(smem_raw + C::OFF_GZ);   // z damping factors of the chunk
     for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
     __syncthreads();
-    const int n = sh[0];
     bool failed = false;
 
     if (tid >= C::NC) {
         // ------------------------------------------------------------ producer warp
         if (tid == C::NC) {
-            prefetch_tmap(&tm_cur);
-            prefetch_tmap(&tm_prev);
-            prefetch_tmap(&tm_kappa);
+            prefetch_tmap(tm_cur);
+            prefetch_tmap(tm_prev);
+            prefetch_tmap(tm_kappa);
             int a_end = z0, b_end = z0;             // planes issued: A [z0, a_end), B [z0, b_end)
             bool ok = true;
             auto issue_a = [&](int p) {
@@ -120,7 +136,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
                     return;
                 }
                 mbar_arrive_expect_tx(&fullA[s], C::SLOT_A * 4);
-                tma_load_3d(ringA + s * C::SLOT_A, &tm_cur, &fullA[s], x0 - R, y0 - R, p);
+                tma_load_3d(ringA + s * C::SLOT_A, tm_cur, &fullA[s], x0 - R, y0 - R, p);
                 a_end = p + 1;
             };
             auto issue_b = [&](int k) {
@@ -131,8 +147,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
                 }
                 mbar_arrive_expect_tx(&fullB[s], C::SLOT_B * 4);
                 float *dst = ringB + s * C::SLOT_B;
-                tma_load_3d(dst, &tm_prev, &fullB[s], x0, y0, k);
-                tma_load_3d(dst + TX * TY, &tm_kappa, &fullB[s], x0, y0, k);
+                tma_load_3d(dst, tm_prev, &fullB[s], x0, y0, k);
+                tma_load_3d(dst + TX * TY, tm_kappa, &fullB[s], x0, y0, k);
                 b_end = k + 1;
             };
             for (int p = z0; ok && p < min(z0 + R, zend); ++p) issue_a(p);
@@ -164,7 +180,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             const int p = z0 - R + m;
-            q[m] = (act && p >= 0) ? ld_nc_na(a.cur + p * a.plane + rowoff) : zero4;
+            q[m] = (act && p >= 0) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
         }
         bool ok = true;
 #pragma unroll
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) o[e] *= gu[e] * gyz;
 
-                float *dst = a.prev + k * a.plane + rowoff;
+                float *dst = prev + k * a.plane + rowoff;
                 if (gxi + 3 < a.nx) {
                     st_cs(dst, make_float4(o[0], o[1], o[2], o[3]));
                 } else {
@@ -324,6 +340,44 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     }
 }
 
+
+template <int R, int TX, int TY, int LA>
+__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+    iso_sweep_kernel(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
+                     const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ IsoArgs a)
+{
+    using C = IsoCfg<R, TX, TY, LA>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int n = step_prologue(a.st, a.ncta, 0x7fffffff, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
+    iso_body<R, TX, TY, LA>(&tm_cur, &tm_prev, &tm_kappa, a, a.prev, a.cur, n, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched step: one launch advances every member shot of a batch by one step.
+// Block b takes work item items[b] = (shot, tile x, tile y, z chunk); the shot's
+// time index selects which of its two wavefield buffers holds u^n, so a graph
+// of these launches replays without per-step arguments.  Shots that reached
+// their last step skip their items.
+template <int R, int TX, int TY, int LA>
+__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+    iso_batch_kernel(const int4 *__restrict__ items, const BatchShot *__restrict__ shots)
+{
+    using C = IsoCfg<R, TX, TY, LA>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int4 it = items[blockIdx.x];
+    const BatchShot &b = shots[it.x];
+    // The shot's parameters are read every plane: keep a copy in shared memory
+    // (after the largest z-chunk table) rather than in global memory.
+    IsoArgs *sa = reinterpret_cast<IsoArgs *>(smem_raw + C::OFF_GZ + 4 * kMaxChunk);
+    static_assert(sizeof(IsoArgs) % 16 == 0, "IsoArgs copies as int4");
+    for (int i = threadIdx.x; i < (int)(sizeof(IsoArgs) / 16); i += blockDim.x)
+        reinterpret_cast<int4 *>(sa)[i] = reinterpret_cast<const int4 *>(&b.a)[i];
+    const int n = step_prologue(b.a.st, b.ncta, b.n_end, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
+    if (n < 0) return;
+    const int c = b.cur0 ^ ((n - b.n0) & 1);      // buffer holding u^n
+    iso_body<R, TX, TY, LA>(&b.halo[c], &b.tile[c ^ 1], &b.kappa, *sa, b.buf[c ^ 1], b.buf[c], n, it.y, it.z,
+                            it.w);
+}
+
 // ---------------------------------------------------------------------------
 
 template <int R, int TX, int TY, int LA>
@@ -348,6 +402,26 @@ static cudaError_t launch_t(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <int R, int TX, int TY, int LA>
+static cudaError_t launch_b(const int4 *items, int nitems, const BatchShot *shots, int max_zchunk, cudaStream_t s)
+{
+    using C = IsoCfg<R, TX, TY, LA>;
+    constexpr int smem = C::SMEM + 4 * kMaxChunk + (int)sizeof(IsoArgs);
+    (void)max_zchunk;
+    static bool attr_set[64] = {};   // per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(iso_batch_kernel<R, TX, TY, LA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    if (nitems <= 0) return cudaSuccess;
+    iso_batch_kernel<R, TX, TY, LA><<<nitems, C::NT, smem, s>>>(items, shots);
+    return cudaGetLastError();
+}
+
 // The (R, tile, lookahead) combinations built into the library.
 #define FD_ISO_CONFIGS(X) \
     X(4, 64, 16, 3)       \
@@ -366,6 +440,17 @@ cudaError_t launch_iso(int R, const Launch &L, const IsoMaps &tm, const IsoArgs 
     if (R == R_ && L.tx == TX_ && L.ty == TY_ && L.lookahead == LA_) return launch_t<R_, TX_, TY_, LA_>(tm, a, s);
     FD_ISO_CONFIGS(FD_ISO_CASE)
 #undef FD_ISO_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_iso_batch(int R, const Launch &L, const int4 *items, int nitems, const BatchShot *shots,
+                             int max_zchunk, cudaStream_t s)
+{
+#define FD_ISO_BCASE(R_, TX_, TY_, LA_)                                \
+    if (R == R_ && L.tx == TX_ && L.ty == TY_ && L.lookahead == LA_) \
+        return launch_b<R_, TX_, TY_, LA_>(items, nitems, shots, max_zchunk, s);
+    FD_ISO_CONFIGS(FD_ISO_BCASE)
+#undef FD_ISO_BCASE
     return cudaErrorInvalidConfiguration;
 }
 

@@ -38,6 +38,8 @@ EXPORTS = [
     "fd_set_graph", "fd_read_receivers", "fd_get_state", "fd_set_state", "fd_field",
     "fd_set_launch", "fd_time_index", "fd_sync", "fd_destroy_grid", "fd_last_error",
     "fd_iso_step_static",
+    "fd_batch_create", "fd_batch_set_launch", "fd_batch_set_graph", "fd_batch_add", "fd_batch_remove",
+    "fd_batch_steps_left", "fd_batch_run", "fd_batch_destroy",
 ]
 
 
@@ -102,6 +104,14 @@ def lib() -> ctypes.CDLL:
             "fd_destroy_grid": [_vp],
             "fd_last_error": [ctypes.c_char_p, ctypes.c_size_t],
             "fd_iso_step_static": [D, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _d, _vp],
+            "fd_batch_create": [_vp, ctypes.POINTER(_vp)],
+            "fd_batch_set_launch": [_vp, _i, _i, _i, _i, _i],
+            "fd_batch_set_graph": [_vp, _i],
+            "fd_batch_add": [_vp, _vp, _i],
+            "fd_batch_remove": [_vp, _vp],
+            "fd_batch_steps_left": [_vp, _vp, ctypes.POINTER(_i)],
+            "fd_batch_run": [_vp, _i, ctypes.POINTER(_i)],
+            "fd_batch_destroy": [_vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -252,6 +262,44 @@ def fd_iso_step_static(d: fd_desc, u_cur, u_prev, kappa, n, src=None, freq_hz=15
                                     sx, sy, sz, freq_hz, t0, amp, stream))
 
 
+def fd_batch_create(stream: int) -> int:
+    out = _vp()
+    _check(lib().fd_batch_create(stream, ctypes.byref(out)))
+    return out.value
+
+
+def fd_batch_set_launch(b, radius, tx, ty, zchunk, lookahead) -> None:
+    _check(lib().fd_batch_set_launch(b, radius, tx, ty, zchunk, lookahead))
+
+
+def fd_batch_set_graph(b, steps: int) -> None:
+    _check(lib().fd_batch_set_graph(b, steps))
+
+
+def fd_batch_add(b, g, nsteps: int) -> None:
+    _check(lib().fd_batch_add(b, g, nsteps))
+
+
+def fd_batch_remove(b, g) -> None:
+    _check(lib().fd_batch_remove(b, g))
+
+
+def fd_batch_steps_left(b, g) -> int:
+    n = _i()
+    _check(lib().fd_batch_steps_left(b, g, ctypes.byref(n)))
+    return n.value
+
+
+def fd_batch_run(b, max_steps: int) -> int:
+    n = _i()
+    _check(lib().fd_batch_run(b, max_steps, ctypes.byref(n)))
+    return n.value
+
+
+def fd_batch_destroy(b) -> None:
+    _check(lib().fd_batch_destroy(b))
+
+
 # ---- one shot on the GPU ---------------------------------------------------------
 
 @dataclass
@@ -390,7 +438,7 @@ class Grid:
             pass
 
 
-def grid_from_shot(shot, device=None, nt_cap=None, model=True) -> Grid:
+def grid_from_shot(shot, device=None, nt_cap=None, model=True, receivers=True) -> Grid:
     """Grid for a ``synth.Shot`` with its model, source and receivers set."""
     g = Grid(GridSpec.from_shot(shot), device=device)
     if model:
@@ -398,6 +446,6 @@ def grid_from_shot(shot, device=None, nt_cap=None, model=True) -> Grid:
     if shot.src is not None:
         g.add_source(*shot.src, freq_hz=shot.src_f, t0=shot.src_t0, amp=shot.src_amp,
                      inject_q=shot.src_into_q)
-    if shot.receivers is not None and len(shot.receivers):
+    if receivers and shot.receivers is not None and len(shot.receivers):
         g.set_receivers(shot.receivers, shot.nsteps if nt_cap is None else nt_cap)
     return g

@@ -168,6 +168,25 @@ def vti_shot(n: int = 512, nsteps: int = 1000, seed: int = 3, r_xy: int = 12, r_
     return s
 
 
+def survey_shots(count: int = 64, seed: int = 2024, n_lo: int = 96, n_hi: int = 320,
+                 steps_lo: int = 300, steps_hi: int = 1500, radii=(4,), with_model: bool = True):
+    """Independent shots of a survey: cubic grids n ~ U{n_lo..n_hi}, step counts
+    ~ U{steps_lo..steps_hi}, radius drawn from `radii`, each with its own seeded
+    layered model, damping layer, source and surface receivers (as
+    ``layered_shot``)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    steps = rng.integers(steps_lo, steps_hi + 1, size=count)
+    rs = rng.choice(np.asarray(radii), size=count)
+    out = []
+    for i in range(count):
+        s = layered_shot(int(ns[i]), int(rs[i]), nsteps=int(steps[i]), seed=seed * 1000 + i,
+                         with_model=with_model)
+        s.name = f"survey{seed}_{i}_n{ns[i]}_r{rs[i]}"
+        out.append(s)
+    return out
+
+
 # 0.5 * 2 / sqrt(v_max^2 (1.5 * 2 sigma_12 + sigma_8 / 0.81)) * h at h = 10 m,
 # v_max = 4725 m/s (sigma_R as in COURANT_LIMIT).  A literal; a test checks it
 # against the oracle's stability bound for the generated tables.
