@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="iso512_r4", choices=sorted(WORKLOADS) + ["survey64"])
+    ap.add_argument("--workload", default="iso512_r4", choices=sorted(WORKLOADS) + ["survey64", "serve"])
+    ap.add_argument("--requests", type=int, default=120, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=96.0, help="serve: HBM budget of resident shots")
     ap.add_argument("--n", type=int, default=512, help="grid points per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -407,6 +410,44 @@ def run_survey(args):
     return 0 if same else 1
 
 
+def run_serve(args):
+    """A Poisson stream of shot requests (cubic 128^3..400^3, 500..2000 steps,
+    radius 4 or 8, own layered models drawn on the GPU) served by the
+    continuous-batching server (HBM budget, resident wavefields) vs a FIFO loop
+    of one shot at a time; same requests, same arrival clock."""
+    import torch
+
+    from paper_1410_1387_gb300 import serve, synth
+
+    torch.cuda.set_device(0)
+    reqs = synth.poisson_requests(args.requests, rate=args.rate, seed=77)
+    pts = sum(r.n ** 3 * r.steps for r in reqs)
+    server = serve.ShotServer(int(args.budget_gb * 2 ** 30), steps_per_iter=25)
+    t0 = time.perf_counter()
+    res_s = server.serve(reqs, realtime=True)
+    wall_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    res_f = serve.fifo_loop(reqs, realtime=True)
+    wall_f = time.perf_counter() - t0
+    s, f = serve.summary(res_s, wall_s), serve.summary(res_f, wall_f)
+    line = {
+        "metric": METRIC, "value": s["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": None,
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": "serve_poisson", "requests": len(reqs), "rate_per_s": args.rate,
+                   "grids": "cubic, n ~ U{128..400}", "steps": "U{500..2000}", "radius": "4 or 8",
+                   "budget_gb": args.budget_gb, "steps_per_iter": 25,
+                   "max_resident_points": server.max_points,
+                   "offered_points_per_s": pts / max(r.arrival for r in reqs)},
+        "served": s, "fifo_loop": f, "max_resident": server.max_resident,
+        "speedup_vs_fifo": f["makespan_s"] / s["makespan_s"],
+        "p99_ratio_fifo_over_served": f["p99_latency_s"] / s["p99_latency_s"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -415,6 +456,8 @@ def main():
     __graft_entry__.build()
     if args.workload == "survey64":
         return run_survey(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -245,7 +245,9 @@ int fd_batch_set_launch(fd_batch_t *b, int radius, int tx, int ty, int zchunk, i
 int fd_batch_set_graph(fd_batch_t *b, int steps);
 
 /* Add grid g (isotropic, model set) to run `nsteps` more steps in the batch.
-   The grid stays owned by the caller and must outlive its membership. */
+   If g uses another stream, that stream is synchronised first so that its
+   setup precedes the batch launches.  The grid stays owned by the caller and
+   must outlive every batch launch enqueued while it was a member. */
 int fd_batch_add(fd_batch_t *b, fd_grid_t *g, int nsteps);
 
 /* Detach g (finished, or cancelled between runs). */

@@ -263,20 +263,24 @@ int check_dev_status(fd_grid *g)
     return FD_OK;
 }
 
-int upload(void **dst, const void *src, size_t bytes)
+// Replace a small device table, stream-ordered on s: the old table is freed
+// after the work already enqueued on s, and no call synchronises the device
+// (a server creates and destroys grids while other shots run).
+int upload(void **dst, const void *src, size_t bytes, cudaStream_t s)
 {
     if (*dst) {
-        cudaFree(*dst);
+        cudaFreeAsync(*dst, s);
         *dst = nullptr;
     }
     if (bytes == 0) return FD_OK;
-    cudaError_t e = cudaMalloc(dst, bytes);
+    cudaError_t e = cudaMallocAsync(dst, bytes, s);
     if (e != cudaSuccess) {
         *dst = nullptr;
         cudaGetLastError();
         return fail(FD_ERR_NO_MEMORY, "table allocation of %zu bytes failed", bytes);
     }
-    CU(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "table upload");
+    // pageable source: staged before the call returns, so `src` may go away
+    CU(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s), "table upload");
     return FD_OK;
 }
 
@@ -300,7 +304,7 @@ int set_source_table(fd_grid *g, int ix, int iy, int iz, const std::vector<doubl
     const double scale = d.dt * d.dt / source_volume(g, iz);
     std::vector<float> tab(s.size());
     for (size_t i = 0; i < s.size(); ++i) tab[i] = (float)(s[i] * scale);
-    int rc = upload(reinterpret_cast<void **>(&g->src_tab), tab.data(), tab.size() * sizeof(float));
+    int rc = upload(reinterpret_cast<void **>(&g->src_tab), tab.data(), tab.size() * sizeof(float), g->stream);
     if (rc) return rc;
     g->src_len = (int)tab.size();
     g->sx = ix; g->sy = iy; g->sz = iz;
@@ -402,10 +406,10 @@ int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stre
         fd_destroy_grid(g);
         return code;
     };
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&g->st), sizeof(DevState));
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&g->st), sizeof(DevState), g->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "status block allocation"));
-    e = cudaMallocHost(reinterpret_cast<void **>(&g->st_host), sizeof(DevState));
-    if (e != cudaSuccess) return bail(cuda_fail(e, "pinned status allocation"));
+    g->st_host = new (std::nothrow) DevState;
+    if (!g->st_host) return bail(fail(FD_ERR_NO_MEMORY, "host allocation failed"));
     e = cudaMemsetAsync(g->st, 0, sizeof(DevState), g->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "status clear"));
     e = cudaMemsetAsync(g->arena, 0, (size_t)lay.nfields * lay.field_bytes, g->stream);
@@ -428,7 +432,7 @@ int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stre
         z_weights(d->nz, d->r_z, g->dzk.empty() ? nullptr : g->dzk.data(), g->d.dz, tab.data());
         g->zrow_max = z_row_abs_max(tab.data(), d->nz, d->r_z);
         std::vector<float> tf(tab.begin(), tab.end());
-        rc = upload(reinterpret_cast<void **>(&g->ztab), tf.data(), tf.size() * sizeof(float));
+        rc = upload(reinterpret_cast<void **>(&g->ztab), tf.data(), tf.size() * sizeof(float), g->stream);
         if (rc) return bail(rc);
     }
     // damping profiles (Cerjan), padded to the pitch for 128-bit loads
@@ -436,9 +440,9 @@ int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stre
     for (int i = 0; i < d->nx; ++i) px[i] = (float)cerjan(i, d->nx, d->sponge_width, d->sponge_a);
     for (int j = 0; j < d->ny; ++j) py[j] = (float)cerjan(j, d->ny, d->sponge_width, d->sponge_a);
     for (int k = 0; k < d->nz; ++k) pz[k] = (float)cerjan(k, d->nz, d->sponge_width, d->sponge_a);
-    if ((rc = upload(reinterpret_cast<void **>(&g->gx), px.data(), px.size() * 4)) ||
-        (rc = upload(reinterpret_cast<void **>(&g->gy), py.data(), py.size() * 4)) ||
-        (rc = upload(reinterpret_cast<void **>(&g->gz), pz.data(), pz.size() * 4)))
+    if ((rc = upload(reinterpret_cast<void **>(&g->gx), px.data(), px.size() * 4, g->stream)) ||
+        (rc = upload(reinterpret_cast<void **>(&g->gy), py.data(), py.size() * 4, g->stream)) ||
+        (rc = upload(reinterpret_cast<void **>(&g->gz), pz.data(), pz.size() * 4, g->stream)))
         return bail(rc);
 
     rc = set_launch(g, default_launch(d));
@@ -586,7 +590,7 @@ int fd_set_receivers(fd_grid_t *g, const int *idx, int nrec, float *trace_dev, i
         g->lat.t0 = g->n;
         g->lat.cap = nt_cap;
     } else {
-        int rc = upload(reinterpret_cast<void **>(&g->rec_idx), idx, (size_t)nrec * 3 * sizeof(int));
+        int rc = upload(reinterpret_cast<void **>(&g->rec_idx), idx, (size_t)nrec * 3 * sizeof(int), g->stream);
         if (rc) {
             g->nrec = 0;
             return rc;
@@ -736,13 +740,14 @@ int fd_sync(fd_grid_t *g)
 int fd_destroy_grid(fd_grid_t *g)
 {
     if (!g) return FD_OK;
-    if (g->stream || g->st) cudaStreamSynchronize(g->stream);
     drop_graphs(g);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    // stream-ordered frees: after this grid's enqueued work, without a device-wide sync
     void *bufs[] = {g->st, g->gx, g->gy, g->gz, g->ztab, g->src_tab, g->rec_idx};
     for (void *p : bufs)
-        if (p) cudaFree(p);
-    if (g->st_host) cudaFreeHost(g->st_host);
+        if (p) cudaFreeAsync(p, g->stream);
+    cudaStreamSynchronize(g->stream);
+    delete g->st_host;
     delete g;
     cudaGetLastError();
     return FD_OK;
@@ -850,7 +855,9 @@ int batch_rebuild(fd_batch *b)
             CU(cudaMemcpyAsync(b->d_items + b->off[r], items[r].data(), items[r].size() * sizeof(int4),
                                cudaMemcpyHostToDevice, b->stream),
                "batch work-list upload");
-    CU(cudaStreamSynchronize(b->stream), "batch upload");
+    // No synchronisation: the uploads are ordered on the batch stream after the
+    // launches that read the previous lists, and their pageable sources were
+    // staged before the copy calls returned.
     b->dirty = false;
     batch_drop_graph(b);
     return FD_OK;
@@ -921,6 +928,8 @@ int fd_batch_add(fd_batch_t *b, fd_grid_t *g, int nsteps)
         return fail(FD_ERR_OUT_OF_RANGE, "receiver buffer too small for %d more steps", nsteps);
     for (const auto &m : b->members)
         if (m.g == g) return fail(FD_ERR_INVALID_ARG, "grid is already in the batch");
+    // the grid's own setup (tables, source, state) may sit on another stream
+    if (g->stream != b->stream) CU(cudaStreamSynchronize(g->stream), "member setup");
     b->members.push_back({g, g->n + nsteps});
     b->dirty = true;
     return FD_OK;

@@ -187,6 +187,56 @@ def survey_shots(count: int = 64, seed: int = 2024, n_lo: int = 96, n_hi: int = 
     return out
 
 
+@dataclass
+class Request:
+    """One shot request of a served stream."""
+    rid: int
+    arrival: float          # seconds after the stream starts
+    n: int                  # cubic grid size
+    steps: int
+    radius: int
+    seed: int
+
+
+def poisson_requests(count: int = 1000, rate: float = 20.0, seed: int = 77, n_lo: int = 128,
+                     n_hi: int = 400, steps_lo: int = 500, steps_hi: int = 2000, radii=(4, 8)):
+    """A Poisson stream: exponential inter-arrival times of mean 1/rate, grid
+    sizes, step counts and radii drawn uniformly."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    st = rng.integers(steps_lo, steps_hi + 1, size=count)
+    rs = rng.choice(np.asarray(radii), size=count)
+    return [Request(i, float(t[i]), int(ns[i]), int(st[i]), int(rs[i]), seed * 100003 + i)
+            for i in range(count)]
+
+
+def request_shot(req: Request, receiver_stride: int = 4) -> Shot:
+    """The shot of a request, without its model: layered-shot geometry, every
+    `receiver_stride`-th cell of the surface plane as receivers."""
+    s = layered_shot(req.n, req.radius, nsteps=req.steps, seed=req.seed, with_model=False)
+    s.receivers = receiver_plane(req.n, req.n, s.nb, stride=receiver_stride)
+    s.name = f"req{req.rid}"
+    return s
+
+
+def layered_model_device(n: int, seed: int, device, nlayers: int = 10, vmin: float = 1500.0,
+                         vmax: float = 4500.0, noise: float = 0.05):
+    """Layered model drawn on the GPU (torch's seeded Philox generator) so that a
+    server need not build large models on the host: layer cuts and speeds as
+    ``layered_model``, cell noise from torch.rand."""
+    import torch
+    rng = np.random.default_rng(seed)
+    cuts = np.sort(rng.integers(1, max(n, 2), size=nlayers - 1))
+    speeds = rng.uniform(vmin, vmax, size=nlayers)
+    vk = torch.as_tensor(speeds[np.searchsorted(cuts, np.arange(n), side="right")], dtype=torch.float32,
+                         device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    r = torch.rand((n, n, n), generator=gen, device=device, dtype=torch.float32)
+    return vk[:, None, None] * (1.0 + noise * (2.0 * r - 1.0))
+
+
 # 0.5 * 2 / sqrt(v_max^2 (1.5 * 2 sigma_12 + sigma_8 / 0.81)) * h at h = 10 m,
 # v_max = 4725 m/s (sigma_R as in COURANT_LIMIT).  A literal; a test checks it
 # against the oracle's stability bound for the generated tables.
