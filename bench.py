@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="iso512_r4", choices=sorted(WORKLOADS) + ["survey64", "serve"])
+    ap.add_argument("--workload", default="iso512_r4",
+                    choices=sorted(WORKLOADS) + ["survey64", "serve", "gradient256"])
     ap.add_argument("--requests", type=int, default=120, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
     ap.add_argument("--budget-gb", type=float, default=96.0, help="serve: HBM budget of resident shots")
@@ -448,6 +449,53 @@ def run_serve(args):
     return 0
 
 
+def run_adjoint(args):
+    """Misfit gradient of a 256^3 layered shot (radius 4, 2000 steps, 128 x 128
+    receivers) with respect to the velocity, against data from the same model
+    plus a 10 % Gaussian anomaly: forward with checkpoints every 50 steps, then
+    recompute + adjoint + gradient, all through the C ABI."""
+    import torch
+
+    from paper_1410_1387_gb300 import adjoint, fd, synth
+
+    torch.cuda.set_device(0)
+    n = args.n if args.n != 512 else 256
+    bg, vtrue = synth.gradient_shot(n, nsteps=2000)
+    true = synth.layered_shot(n, 4, nsteps=2000, with_model=False)
+    true.receivers, true.v = bg.receivers, vtrue
+    g = fd.grid_from_shot(true)
+    g.run(true.nsteps)
+    dobs = g.trace.clone()
+    g.close()
+    v = torch.from_numpy(bg.v).cuda()
+    solver = adjoint.AdjointSolver(bg, checkpoint_every=50)
+    solver.forward(v, dobs)          # warm-up (allocations, graphs of the allocator)
+    solver.backward()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, _ = solver.forward(v, dobs)
+    t1 = time.perf_counter()
+    grad = solver.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    pts = bg.points * bg.nsteps
+    gn = grad.double()
+    centre = gn[n // 2 - 10:n // 2 + 10, n // 2 - 10:n // 2 + 10, n // 2 - 10:n // 2 + 10]
+    line = {
+        "metric": METRIC, "value": 1.0 / (t2 - t0), "unit": "gradients/s", "n_gpus": 1, "steps": bg.nsteps,
+        "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": f"gradient{n}_r4", "grid": [n, n, n], "steps": bg.nsteps,
+                   "receivers": len(bg.receivers), "checkpoint_every": 50,
+                   "anomaly": "10 % Gaussian, sigma 15 cells, centre"},
+        "misfit": J, "forward_seconds": t1 - t0, "backward_seconds": t2 - t1,
+        "sweep_points_per_s": 3 * pts / (t2 - t0),
+        "gradient_centre_mean": float(centre.mean()), "gradient_abs_max": float(gn.abs().max()),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -458,6 +506,8 @@ def main():
         return run_survey(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "gradient256":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -218,6 +218,34 @@ int fd_destroy_grid(fd_grid_t *g);
 /* Copy the calling thread's last error message into buf (always terminated). */
 int fd_last_error(char *buf, size_t n);
 
+/* ---- adjoint and velocity gradient -----------------------------------------
+ * For J = 1/2 sum_n sum_r (u^{n+1}(x_r) - dobs[n][r])^2 of an isotropic run
+ * (an extension: the paper computes no gradients; its use is imaging).  The
+ * step of fd_step is x_{n+1} = A x_n + f_n on the stored pair (u^n, u_prev)
+ * with A = [[G (2 + K L), -G^2], [1, 0]], K = (v dt)^2.  Its transpose,
+ * written for z = K G alpha (alpha the adjoint of u), is the same step run
+ * backward in time:
+ *   z_n = G (2 z_{n+1} - G z_{n+2} + K L z_{n+1} + K R^T r_{n-1}),
+ * i.e. fd_step on a second grid with the residuals injected at the receivers,
+ * and dJ/dv = sum_n 2 dt z_{n+1} (L u^n) / sqrt(K).
+ */
+
+/* Additive sources on a lattice (one z plane, row-major, constant strides):
+   at step n, point r gets values_dev[(n - n_set) * nrec + r] added inside the
+   damping bracket (like the Ricker source).  values_dev: device, nt_cap rows,
+   owned by the caller.  nrec = 0 removes them.  Isotropic grids only. */
+int fd_set_injection(fd_grid_t *g, const int *idx_xyz, int nrec, const float *values_dev, int nt_cap);
+
+/* From device traces and data (nt x nrec, row n = step n, g's receiver lattice):
+   inj[m][r] = K(x_r) (traces - dobs)[nt-1-m][r] (device, nt x nrec; the
+   adjoint run's injection rows) and *misfit = J (host; synchronises). */
+int fd_adjoint_source(fd_grid_t *g, const float *traces, const float *dobs, int nt, float *inj,
+                      double *misfit);
+
+/* grad += 2 dt z (L a) / sqrt(K) over g's grid; z, a, grad are device arrays
+   in g's pitched layout (fd_layout).  Asynchronous on g's stream. */
+int fd_grad_accumulate(fd_grid_t *g, const float *z, const float *a, float *grad);
+
 /* ---- batched shots --------------------------------------------------------
  * Many independent isotropic shots (radius 4 or 8, any sizes and step counts)
  * advanced together: each launch performs one time step (Eq. 3, exactly the

@@ -488,6 +488,109 @@ int or_vti_step_points(const or_cfg *c, const float *vz, const float *eps, const
     return 0;
 }
 
+/*
+ * Misfit and velocity gradient of the isotropic run (zero initial state,
+ * source, damping and receivers as in or_iso_run):
+ *   J = 1/2 sum_{n<N} sum_r (u^{n+1}(x_r) - dobs[n][r])^2.
+ * Written in the physical variables of the literal Cerjan recurrence: with
+ * p^n the damped older level, one step is
+ *   u^{n+1} = G (2 u^n - p^n + K L u^n + S_n),   p^{n+1} = G u^n,   K = (v dt)^2,
+ * i.e. x_{n+1} = A x_n + f_n with A = [[G (2 + K L), -G], [G, 0]].  The
+ * adjoint state (alpha, beta) runs backward with the transpose of A (L is
+ * symmetric, G and K diagonal):
+ *   alpha_n = (2 + L K) G alpha_{n+1} + G beta_{n+1} + R^T r_{n-1},
+ *   beta_n  = -G alpha_{n+1},
+ * from alpha_N = R^T r_{N-1}, beta_N = 0 (r_n = data residual of step n), and
+ *   dJ/dK(x) = sum_{n<N} alpha_{n+1}(x) G(x) (L u^n)(x),  dJ/dv = dJ/dK 2 v dt^2.
+ * Stores every forward level: for small grids only.  grad_v may be NULL.
+ */
+int or_iso_misfit_grad(const or_cfg *c, const double *v, const double *dobs, int nsteps, double *J,
+                       double *grad_v)
+{
+    double cw[33], cz[33];
+    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    const size_t N = (size_t)c->nx * (size_t)c->ny * (size_t)c->nz;
+    const size_t B = sizeof(double) * (N ? N : 1);
+    double *U = (double *)calloc((size_t)(nsteps + 1) * (N ? N : 1), sizeof(double));   /* u^0..u^N */
+    double *P = (double *)calloc(N ? N : 1, sizeof(double));
+    double *G = (double *)malloc(B), *K = (double *)malloc(B), *Lu = (double *)malloc(B);
+    double *al = (double *)calloc(N ? N : 1, sizeof(double)), *be = (double *)calloc(N ? N : 1, sizeof(double));
+    double *aln = (double *)malloc(B), *w = (double *)malloc(B), *gk = (double *)calloc(N ? N : 1, sizeof(double));
+    double *res = (double *)malloc(sizeof(double) * (size_t)(nsteps > 0 ? nsteps : 1) * (size_t)(c->nrec > 0 ? c->nrec : 1));
+    if (!U || !P || !G || !K || !Lu || !al || !be || !aln || !w || !gk || !res) {
+        free(U); free(P); free(G); free(K); free(Lu); free(al); free(be); free(aln); free(w); free(gk); free(res);
+        return -2;
+    }
+    for (int k = 0; k < c->nz; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                size_t m = idx(c, i, j, k);
+                G[m] = c->nb > 0 ? sponge_at(c, i, j, k) : 1.0;
+                K[m] = v[m] * c->dt * v[m] * c->dt;
+            }
+    /* forward, keeping every level */
+    double Jsum = 0.0;
+    for (int n = 0; n < nsteps; ++n) {
+        double *u = U + (size_t)n * N, *un = U + (size_t)(n + 1) * N;
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < c->nz; ++k)
+            for (int j = 0; j < c->ny; ++j)
+                for (int i = 0; i < c->nx; ++i) {
+                    size_t m = idx(c, i, j, k);
+                    double L = op_h(c, cw, u, i, j, k) + op_z(c, cz, u, i, j, k);
+                    un[m] = G[m] * (2.0 * u[m] - P[m] + K[m] * L);
+                }
+        if (c->src_on) {
+            size_t s = idx(c, c->sx, c->sy, c->sz);
+            un[s] += G[s] * source_term(c, n);
+        }
+        for (size_t m = 0; m < N; ++m) P[m] = G[m] * u[m];
+        for (int r = 0; r < c->nrec; ++r) {
+            double d = un[idx(c, c->rec[3 * r], c->rec[3 * r + 1], c->rec[3 * r + 2])] -
+                       dobs[(size_t)n * (size_t)c->nrec + (size_t)r];
+            res[(size_t)n * (size_t)c->nrec + (size_t)r] = d;
+            Jsum += 0.5 * d * d;
+        }
+    }
+    *J = Jsum;
+    if (grad_v) {
+        /* backward: alpha_{n} from alpha_{n+1}, beta_{n+1}; gradient term with u^n */
+        for (int n = nsteps; n >= 1; --n) {
+            /* al, be hold (alpha_{n+1}, beta_{n+1}) (zero for n = N) */
+#pragma omp parallel for schedule(static)
+            for (size_t m = 0; m < N; ++m) w[m] = K[m] * G[m] * al[m];
+#pragma omp parallel for schedule(static)
+            for (int k = 0; k < c->nz; ++k)
+                for (int j = 0; j < c->ny; ++j)
+                    for (int i = 0; i < c->nx; ++i) {
+                        size_t m = idx(c, i, j, k);
+                        double Lw = op_h(c, cw, w, i, j, k) + op_z(c, cz, w, i, j, k);
+                        aln[m] = 2.0 * G[m] * al[m] + Lw + G[m] * be[m];
+                    }
+            for (int r = 0; r < c->nrec; ++r)
+                aln[idx(c, c->rec[3 * r], c->rec[3 * r + 1], c->rec[3 * r + 2])] +=
+                    res[(size_t)(n - 1) * (size_t)c->nrec + (size_t)r];
+            for (size_t m = 0; m < N; ++m) {
+                be[m] = -G[m] * al[m];
+                al[m] = aln[m];
+            }
+            /* al = alpha_n: gradient term of step n-1 uses alpha_n and u^{n-1} */
+            const double *u = U + (size_t)(n - 1) * N;
+#pragma omp parallel for schedule(static)
+            for (int k = 0; k < c->nz; ++k)
+                for (int j = 0; j < c->ny; ++j)
+                    for (int i = 0; i < c->nx; ++i) {
+                        size_t m = idx(c, i, j, k);
+                        double L = op_h(c, cw, u, i, j, k) + op_z(c, cz, u, i, j, k);
+                        gk[m] += al[m] * G[m] * L;
+                    }
+        }
+        for (size_t m = 0; m < N; ++m) grad_v[m] = gk[m] * 2.0 * v[m] * c->dt * c->dt;
+    }
+    free(U); free(P); free(G); free(K); free(Lu); free(al); free(be); free(aln); free(w); free(gk); free(res);
+    return 0;
+}
+
 /* Sponge factor G at a cell (product over the three axes). */
 double or_sponge_at(const or_cfg *c, int i, int j, int k)
 {

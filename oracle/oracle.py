@@ -78,6 +78,7 @@ def lib():
             L.or_iso_step_points.argtypes = [P, _F, _F, ctypes.c_int, _I, _D, ctypes.c_int, _D]
             L.or_vti_step_points.argtypes = [P, _F, _F, _F, _F, _F, ctypes.c_int, _I, _D, _D,
                                              ctypes.c_int, _D, _D]
+            L.or_iso_misfit_grad.argtypes = [P, _D, _D, ctypes.c_int, _D, _D]
             L.or_sponge_at.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.or_sponge_at.restype = ctypes.c_double
             L.or_num_threads.restype = ctypes.c_int
@@ -244,6 +245,18 @@ class Problem:
         if rc != 0:
             raise RuntimeError(f"or_vti_run failed: {rc}")
         return p, pprev, q, qprev, tr
+
+    def iso_misfit_grad(self, v, dobs, nsteps, grad=True):
+        """(J, dJ/dv) of the run from rest against data dobs (nsteps, nrec)."""
+        v = _c64(v)
+        dobs = _c64(dobs).reshape(nsteps, self.nrec)
+        J = ctypes.c_double()
+        g = np.zeros(self.shape) if grad else None
+        rc = lib().or_iso_misfit_grad(ctypes.byref(self.cfg), _dp(v), _dp(dobs), nsteps, ctypes.byref(J),
+                                      _dp(g) if grad else None)
+        if rc != 0:
+            raise RuntimeError("or_iso_misfit_grad failed")
+        return J.value, g
 
     def iso_step_points(self, v32, u32, pts, uprev_pts, n):
         """u^{n+1} at the cells pts (M, 3) [ix, iy, iz] from float32 state u^n."""

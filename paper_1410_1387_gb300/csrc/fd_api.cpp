@@ -123,6 +123,9 @@ struct fd_grid {
     bool lattice = false;
     RecLattice lat{};
     int *rec_idx = nullptr;
+    // injection lattice (additive per-step sources, e.g. adjoint residuals)
+    RecLattice inj{};
+    double *d_misfit = nullptr;
     // launch
     Launch L{};
     CUtensorMap tm_halo[2];      // u (p) buffers, box (tx + 2 r_xy) x (ty + 2 r_xy)
@@ -195,6 +198,7 @@ IsoArgs iso_args(const fd_grid *g)
     a.src = Source{g->src_tab, g->src_len, g->sx, g->sy, g->sz, g->into_q};
     a.rec = g->lat;
     a.rec.on = (g->nrec > 0 && g->lattice) ? 1 : 0;
+    a.inj = g->inj;
     a.st = g->st;
     return a;
 }
@@ -251,6 +255,8 @@ int check_ready(fd_grid *g, int nsteps)
     if (g->nrec > 0 && (long long)g->n + nsteps - g->rec_t0 > g->rec_cap)
         return fail(FD_ERR_OUT_OF_RANGE, "receiver buffer holds %d rows; step %d would need row %lld",
                     g->rec_cap, g->n + nsteps - 1, (long long)g->n + nsteps - 1 - g->rec_t0);
+    if (g->inj.on && (long long)g->n + nsteps - g->inj.t0 > g->inj.cap)
+        return fail(FD_ERR_OUT_OF_RANGE, "injection buffer holds %d rows", g->inj.cap);
     return FD_OK;
 }
 
@@ -282,6 +288,33 @@ int upload(void **dst, const void *src, size_t bytes, cudaStream_t s)
     // pageable source: staged before the call returns, so `src` may go away
     CU(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s), "table upload");
     return FD_OK;
+}
+
+// A receiver set that is a row-major lattice on one z plane with constant
+// strides: fills the geometry of L (not its buffer, origin step or capacity).
+bool detect_lattice(const int *idx, int nrec, RecLattice *L)
+{
+    int rnx = 1;
+    while (rnx < nrec && idx[3 * rnx + 1] == idx[1]) ++rnx;
+    const int rny = nrec / rnx;
+    const int rsx = rnx > 1 ? idx[3] - idx[0] : 1;
+    const int rsy = rny > 1 ? idx[3 * rnx + 1] - idx[1] : 1;
+    if (rny * rnx != nrec || rsx <= 0 || rsy <= 0) return false;
+    for (int r = 0; r < nrec; ++r) {
+        const int ry = r / rnx, rx = r % rnx;
+        if (idx[3 * r] != idx[0] + rx * rsx || idx[3 * r + 1] != idx[1] + ry * rsy || idx[3 * r + 2] != idx[2])
+            return false;
+    }
+    *L = RecLattice{};
+    L->nrec = nrec;
+    L->rk = idx[2];
+    L->rx0 = idx[0];
+    L->ry0 = idx[1];
+    L->rsx = rsx;
+    L->rsy = rsy;
+    L->rnx = rnx;
+    L->rny = rny;
+    return true;
 }
 
 double source_volume(const fd_grid *g, int iz)
@@ -558,19 +591,8 @@ int fd_set_receivers(fd_grid_t *g, const int *idx, int nrec, float *trace_dev, i
         if (i < 0 || i >= d.nx || j < 0 || j >= d.ny || k < 0 || k >= d.nz)
             return fail(FD_ERR_INVALID_ARG, "receiver %d at (%d, %d, %d) outside the grid", r, i, j, k);
     }
-    // lattice detection: one plane, row-major, constant strides
-    bool lat = true;
-    int rnx = 1;
-    while (rnx < nrec && idx[3 * rnx + 1] == idx[1]) ++rnx;
-    const int rny = nrec / rnx;
-    const int rsx = rnx > 1 ? idx[3] - idx[0] : 1;
-    const int rsy = rny > 1 ? idx[3 * rnx + 1] - idx[1] : 1;
-    if (rny * rnx != nrec || rsx <= 0 || rsy <= 0) lat = false;
-    for (int r = 0; lat && r < nrec; ++r) {
-        const int ry = r / rnx, rx = r % rnx;
-        if (idx[3 * r] != idx[0] + rx * rsx || idx[3 * r + 1] != idx[1] + ry * rsy || idx[3 * r + 2] != idx[2])
-            lat = false;
-    }
+    RecLattice L{};
+    const bool lat = detect_lattice(idx, nrec, &L);
     g->lattice = lat;
     g->nrec = nrec;
     g->trace = trace_dev;
@@ -578,15 +600,8 @@ int fd_set_receivers(fd_grid_t *g, const int *idx, int nrec, float *trace_dev, i
     g->rec_t0 = g->n;
     g->lat = RecLattice{};
     if (lat) {
+        g->lat = L;
         g->lat.trace = trace_dev;
-        g->lat.nrec = nrec;
-        g->lat.rk = idx[2];
-        g->lat.rx0 = idx[0];
-        g->lat.ry0 = idx[1];
-        g->lat.rsx = rsx;
-        g->lat.rsy = rsy;
-        g->lat.rnx = rnx;
-        g->lat.rny = rny;
         g->lat.t0 = g->n;
         g->lat.cap = nt_cap;
     } else {
@@ -600,6 +615,69 @@ int fd_set_receivers(fd_grid_t *g, const int *idx, int nrec, float *trace_dev, i
 }
 
 int fd_step(fd_grid_t *g) { return fd_run(g, 1); }
+
+int fd_set_injection(fd_grid_t *g, const int *idx, int nrec, const float *values_dev, int nt_cap)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    drop_graphs(g);
+    if (nrec == 0) {
+        g->inj = RecLattice{};
+        return FD_OK;
+    }
+    if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "injection lattices are isotropic-only");
+    if (nrec < 0 || !idx || !values_dev || nt_cap < 0) return fail(FD_ERR_INVALID_ARG, "bad injection arguments");
+    const fd_desc &d = g->d;
+    for (int r = 0; r < nrec; ++r) {
+        const int i = idx[3 * r], j = idx[3 * r + 1], k = idx[3 * r + 2];
+        if (i < 0 || i >= d.nx || j < 0 || j >= d.ny || k < 0 || k >= d.nz)
+            return fail(FD_ERR_INVALID_ARG, "injection point %d at (%d, %d, %d) outside the grid", r, i, j, k);
+    }
+    RecLattice L{};
+    if (!detect_lattice(idx, nrec, &L))
+        return fail(FD_ERR_UNSUPPORTED, "injection points must form a row-major lattice on one plane");
+    L.trace = const_cast<float *>(values_dev);
+    L.t0 = g->n;
+    L.cap = nt_cap;
+    L.on = 1;
+    g->inj = L;
+    return FD_OK;
+}
+
+int fd_adjoint_source(fd_grid_t *g, const float *traces, const float *dobs, int nt, float *inj, double *misfit)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "the adjoint is isotropic-only");
+    if (!g->model_set) return fail(FD_ERR_BAD_STATE, "no model");
+    if (g->nrec <= 0 || !g->lattice)
+        return fail(FD_ERR_BAD_STATE, "the grid needs receivers on a lattice (they define the adjoint sources)");
+    if (nt < 0 || (nt > 0 && (!traces || !dobs || !inj)) || !misfit) return fail(FD_ERR_INVALID_ARG, "bad arguments");
+    if (!g->d_misfit) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&g->d_misfit), sizeof(double), g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "misfit allocation");
+    }
+    CU(cudaMemsetAsync(g->d_misfit, 0, sizeof(double), g->stream), "misfit clear");
+    if (nt > 0) {
+        cudaError_t e = launch_adjoint_source(g->lat, g->model[0], g->lay.pitch, (long long)g->lay.pitch * g->d.ny,
+                                              traces, dobs, nt, inj, g->d_misfit, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint source kernel");
+    }
+    CU(cudaMemcpyAsync(misfit, g->d_misfit, sizeof(double), cudaMemcpyDeviceToHost, g->stream), "misfit copy");
+    CU(cudaStreamSynchronize(g->stream), "stream synchronize");
+    return FD_OK;
+}
+
+int fd_grad_accumulate(fd_grid_t *g, const float *z, const float *a, float *grad)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "the adjoint is isotropic-only");
+    if (!g->model_set) return fail(FD_ERR_BAD_STATE, "no model");
+    if (!z || !a || !grad) return fail(FD_ERR_INVALID_ARG, "NULL field");
+    if (g->d.ny > 65535 || g->d.nz > 65535) return fail(FD_ERR_UNSUPPORTED, "grid too large for the gradient kernel");
+    const IsoArgs w = iso_args(g);
+    cudaError_t e = launch_grad(w, g->d.r_xy, g->d.dt, z, a, grad, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient kernel");
+    return FD_OK;
+}
 
 int fd_set_graph(fd_grid_t *g, int steps)
 {
@@ -743,7 +821,7 @@ int fd_destroy_grid(fd_grid_t *g)
     drop_graphs(g);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     // stream-ordered frees: after this grid's enqueued work, without a device-wide sync
-    void *bufs[] = {g->st, g->gx, g->gy, g->gz, g->ztab, g->src_tab, g->rec_idx};
+    void *bufs[] = {g->st, g->gx, g->gy, g->gz, g->ztab, g->src_tab, g->rec_idx, g->d_misfit};
     for (void *p : bufs)
         if (p) cudaFreeAsync(p, g->stream);
     cudaStreamSynchronize(g->stream);

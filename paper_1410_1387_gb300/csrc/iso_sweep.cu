@@ -287,6 +287,21 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 &&
                     n < a.src.len)
                     o[a.src.sx - gxi] += a.src.tab[n];
+                if (a.inj.on && k == a.inj.rk) {
+                    // lattice of additive sources (the adjoint's receiver residuals)
+                    const int ry = gyi - a.inj.ry0;
+                    const int row = n - a.inj.t0;
+                    if (ry >= 0 && ry % a.inj.rsy == 0 && ry / a.inj.rsy < a.inj.rny && row >= 0 &&
+                        row < a.inj.cap) {
+                        const float *irow = a.inj.trace + (long long)row * a.inj.nrec +
+                                            (long long)(ry / a.inj.rsy) * a.inj.rnx;
+                        for (int e = 0; e < 4; ++e) {
+                            const int rx = gxi + e - a.inj.rx0;
+                            if (gxi + e < a.nx && rx >= 0 && rx % a.inj.rsx == 0 && rx / a.inj.rsx < a.inj.rnx)
+                                o[e] += irow[rx / a.inj.rsx];
+                        }
+                    }
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) o[e] *= gu[e] * gyz;
 

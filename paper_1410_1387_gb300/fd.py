@@ -40,6 +40,7 @@ EXPORTS = [
     "fd_iso_step_static",
     "fd_batch_create", "fd_batch_set_launch", "fd_batch_set_graph", "fd_batch_add", "fd_batch_remove",
     "fd_batch_steps_left", "fd_batch_run", "fd_batch_destroy",
+    "fd_set_injection", "fd_adjoint_source", "fd_grad_accumulate",
 ]
 
 
@@ -112,6 +113,9 @@ def lib() -> ctypes.CDLL:
             "fd_batch_steps_left": [_vp, _vp, ctypes.POINTER(_i)],
             "fd_batch_run": [_vp, _i, ctypes.POINTER(_i)],
             "fd_batch_destroy": [_vp],
+            "fd_set_injection": [_vp, _vp, _i, _vp, _i],
+            "fd_adjoint_source": [_vp, _vp, _vp, _i, _vp, ctypes.POINTER(ctypes.c_double)],
+            "fd_grad_accumulate": [_vp, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -260,6 +264,20 @@ def fd_iso_step_static(d: fd_desc, u_cur, u_prev, kappa, n, src=None, freq_hz=15
     t0 = 1.0 / freq_hz if t0 is None else t0
     _check(lib().fd_iso_step_static(ctypes.byref(d), _ptr(u_cur), _ptr(u_prev), _ptr(kappa), n,
                                     sx, sy, sz, freq_hz, t0, amp, stream))
+
+
+def fd_set_injection(g, idx, nrec, values_dev, nt_cap) -> None:
+    _check(lib().fd_set_injection(g, _ptr(idx), nrec, _ptr(values_dev), nt_cap))
+
+
+def fd_adjoint_source(g, traces, dobs, nt, inj) -> float:
+    J = ctypes.c_double()
+    _check(lib().fd_adjoint_source(g, _ptr(traces), _ptr(dobs), nt, _ptr(inj), ctypes.byref(J)))
+    return J.value
+
+
+def fd_grad_accumulate(g, z, a, grad) -> None:
+    _check(lib().fd_grad_accumulate(g, _ptr(z), _ptr(a), _ptr(grad)))
 
 
 def fd_batch_create(stream: int) -> int:
@@ -424,6 +442,14 @@ class Grid:
         off = ptr - self.arena.data_ptr()
         nbytes = s.nz * s.ny * pitch * 4
         return self.arena[off:off + nbytes].view(torch.float32).view(s.nz, s.ny, pitch)
+
+    def model_view(self, m: int = 0):
+        """A (nz, ny, pitch) torch view of model buffer m (kappa; VTI: kx, kn, kz)."""
+        torch = self.torch
+        s, lay = self.spec, self.layout
+        off = self.arena_ptr - self.arena.data_ptr() + (lay.nfields + m) * lay.field_bytes
+        nbytes = s.nz * s.ny * lay.pitch * 4
+        return self.arena[off:off + nbytes].view(torch.float32).view(s.nz, s.ny, lay.pitch)
 
     def close(self):
         if getattr(self, "h", None):

@@ -187,6 +187,22 @@ def survey_shots(count: int = 64, seed: int = 2024, n_lo: int = 96, n_hi: int = 
     return out
 
 
+def gradient_shot(n: int = 256, nsteps: int = 2000, seed: int = 5, amp: float = 0.10, sigma: float = 15.0):
+    """Gradient workload: an n^3 layered background (radius 4, damping layer,
+    source 10 cells below it) with receivers on every 2nd cell of the first
+    plane below the damping layer ((n/2)^2 of them), and the true model =
+    background x (1 + amp exp(-|x - c|^2 / (2 sigma^2))), a Gaussian anomaly at
+    the centre.  Returns (background shot, true velocity)."""
+    s = layered_shot(n, 4, nsteps=nsteps, seed=seed)
+    s.receivers = receiver_plane(n, n, s.nb, stride=2)
+    c = (n - 1) / 2.0
+    ax = (np.arange(n) - c) ** 2
+    bump = np.exp(-(ax[:, None, None] + ax[None, :, None] + ax[None, None, :]) / (2.0 * sigma * sigma))
+    vtrue = (s.v * (1.0 + amp * bump)).astype(np.float32)
+    s.name = f"grad{n}_r4"
+    return s, vtrue
+
+
 @dataclass
 class Request:
     """One shot request of a served stream."""
