@@ -266,6 +266,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    from paper_1410_1387_gb300 import dist as fdist
     from paper_1410_1387_gb300 import fd
 
     world, rank, local = dist_setup(args)
@@ -299,9 +300,7 @@ def run_ours(args):
     el_ms = ev0.elapsed_time(ev1)
     if world > 1:
         dist.barrier()
-        t = torch.tensor([el_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
+    el_ms = fdist.max_over_ranks(el_ms, dev)
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -332,11 +331,7 @@ def run_ours(args):
                             del_h.data_ptr() if del_h is not None else None, fd.FD_PTR_HOST)
             fd.fd_run(g.h, nsh)
             fd.fd_read_receivers(g.h, 0, nsh, tr_h.data_ptr(), fd.FD_PTR_HOST)
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = fdist.max_over_ranks(time.perf_counter() - t0, dev)
         g.close()
         nmodel = 3 if shot.mode == "vti" else 1
         e2e = {"value": pts * nsh * world / e2e_s, "unit": UNIT,
