@@ -1004,6 +1004,7 @@ int fd_batch_add(fd_batch_t *b, fd_grid_t *g, int nsteps)
         return fail(FD_ERR_UNSUPPORTED, "batched shots need receivers on a lattice of one plane");
     if (g->nrec > 0 && (long long)g->n + nsteps - g->rec_t0 > g->rec_cap)
         return fail(FD_ERR_OUT_OF_RANGE, "receiver buffer too small for %d more steps", nsteps);
+    if (g->inj.on) return fail(FD_ERR_UNSUPPORTED, "batched shots take no injection lattice");
     for (const auto &m : b->members)
         if (m.g == g) return fail(FD_ERR_INVALID_ARG, "grid is already in the batch");
     // the grid's own setup (tables, source, state) may sit on another stream

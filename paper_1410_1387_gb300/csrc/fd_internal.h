@@ -19,7 +19,9 @@ struct DevState {
     float kxmax;
     unsigned int bad;       // count of invalid model values
     unsigned int eps_lt_delta;
-    int pad[8];
+    unsigned int work;      // next work item of a persistent sweep (0 between launches)
+    unsigned int exited;    // CTAs of the current launch that have finished
+    int pad[6];
 };
 static_assert(sizeof(DevState) == 64, "status block size");
 constexpr int kErrTmaTimeout = 1;
@@ -90,15 +92,15 @@ struct Launch {
 constexpr int kMaxChunk = 1024;
 
 // Planes per CTA: enough CTAs (about 2048) for several waves over 152 SMs, at
-// least 16 planes per chunk (small grids) so that priming the z queue stays a
-// small share, and at most kMaxChunk.
+// least 32 planes per chunk (measured: shorter chunks lose more to priming the
+// z queue and filling the pipeline than they gain in waves), at most kMaxChunk.
 inline int default_zchunk(const Launch &L, int nx, int ny, int nz)
 {
     const long tiles = (long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
     long chunks = (2048 + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
     int zc = (int)((nz + chunks - 1) / chunks);
-    const int lo = nz < 16 ? nz : 16;
+    const int lo = nz < 32 ? nz : 32;
     zc = zc < lo ? lo : zc;
     return zc > kMaxChunk ? kMaxChunk : zc;
 }

@@ -79,7 +79,9 @@ __device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_
 }
 
 // One CTA's work: tile (bx, by), z chunk bz, of the step u^n -> u^{n+1}.
-template <int R, int TX, int TY, int LA>
+// INJ compiles in the injection lattice (adjoint runs only: the extra branch
+// in the store path costs about 6 % when present).
+template <int R, int TX, int TY, int LA, bool INJ>
 __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtensorMap *tm_prev,
                                          const CUtensorMap *tm_kappa, const IsoArgs &a, float *prev,
                                          const float *cur, const int n, const int bx, const int by, const int bz)
@@ -287,7 +289,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 &&
                     n < a.src.len)
                     o[a.src.sx - gxi] += a.src.tab[n];
-                if (a.inj.on && k == a.inj.rk) {
+                if (INJ && k == a.inj.rk) {
                     // lattice of additive sources (the adjoint's receiver residuals)
                     const int ry = gyi - a.inj.ry0;
                     const int row = n - a.inj.t0;
@@ -356,7 +358,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 }
 
 
-template <int R, int TX, int TY, int LA>
+template <int R, int TX, int TY, int LA, bool INJ>
 __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     iso_sweep_kernel(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
                      const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ IsoArgs a)
@@ -364,7 +366,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     using C = IsoCfg<R, TX, TY, LA>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int n = step_prologue(a.st, a.ncta, 0x7fffffff, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
-    iso_body<R, TX, TY, LA>(&tm_cur, &tm_prev, &tm_kappa, a, a.prev, a.cur, n, blockIdx.x, blockIdx.y, blockIdx.z);
+    iso_body<R, TX, TY, LA, INJ>(&tm_cur, &tm_prev, &tm_kappa, a, a.prev, a.cur, n, blockIdx.x, blockIdx.y,
+                                 blockIdx.z);
 }
 
 // Batched step: one launch advances every member shot of a batch by one step.
@@ -389,14 +392,14 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     const int n = step_prologue(b.a.st, b.ncta, b.n_end, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
     if (n < 0) return;
     const int c = b.cur0 ^ ((n - b.n0) & 1);      // buffer holding u^n
-    iso_body<R, TX, TY, LA>(&b.halo[c], &b.tile[c ^ 1], &b.kappa, *sa, b.buf[c ^ 1], b.buf[c], n, it.y, it.z,
-                            it.w);
+    iso_body<R, TX, TY, LA, false>(&b.halo[c], &b.tile[c ^ 1], &b.kappa, *sa, b.buf[c ^ 1], b.buf[c], n, it.y,
+                                   it.z, it.w);
 }
 
 // ---------------------------------------------------------------------------
 
-template <int R, int TX, int TY, int LA>
-static cudaError_t launch_t(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s)
+template <int R, int TX, int TY, int LA, bool INJ>
+static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s)
 {
     using C = IsoCfg<R, TX, TY, LA>;
     constexpr int smem_max = C::SMEM + 4 * kMaxChunk;
@@ -404,7 +407,7 @@ static cudaError_t launch_t(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(iso_sweep_kernel<R, TX, TY, LA>,
+        cudaError_t e = cudaFuncSetAttribute(iso_sweep_kernel<R, TX, TY, LA, INJ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
@@ -413,8 +416,14 @@ static cudaError_t launch_t(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
     const int smem = C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4);
-    iso_sweep_kernel<R, TX, TY, LA><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, a);
+    iso_sweep_kernel<R, TX, TY, LA, INJ><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, a);
     return cudaGetLastError();
+}
+
+template <int R, int TX, int TY, int LA>
+static cudaError_t launch_t(const IsoMaps &tm, const IsoArgs &a, cudaStream_t s)
+{
+    return a.inj.on ? launch_ti<R, TX, TY, LA, true>(tm, a, s) : launch_ti<R, TX, TY, LA, false>(tm, a, s);
 }
 
 template <int R, int TX, int TY, int LA>
