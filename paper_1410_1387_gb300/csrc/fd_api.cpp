@@ -195,6 +195,10 @@ IsoArgs iso_args(const fd_grid *g)
     a.w0 = g->w0;
     std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
     std::memcpy(a.wz, g->wz, sizeof a.wz);
+    for (int l = 0; l <= kMaxR; ++l) {
+        a.wxy2[l] = make_float2(g->wxy[l], g->wxy[l]);
+        a.wz2[l] = make_float2(g->wz[l], g->wz[l]);
+    }
     a.src = Source{g->src_tab, g->src_len, g->sx, g->sy, g->sz, g->into_q};
     a.rec = g->lat;
     a.rec.on = (g->nrec > 0 && g->lattice) ? 1 : 0;
@@ -233,6 +237,7 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
         a.zchunk = g->L.zchunk;
         a.w0 = g->w0;
         std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
+        for (int l = 0; l <= kMaxR; ++l) a.wxy2[l] = make_float2(g->wxy[l], g->wxy[l]);
         a.src = src; a.rec = rec; a.st = g->st;
         const VtiMaps maps{g->tm_halo[cur],    g->tm_tile[2 + cur], g->tm_tile[1 - cur], g->tm_tile[3 - cur],
                            g->tm_model[0],     g->tm_model[1],      g->tm_model[2]};
@@ -464,7 +469,15 @@ int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stre
         std::vector<double> tab((size_t)d->nz * nw);
         z_weights(d->nz, d->r_z, g->dzk.empty() ? nullptr : g->dzk.data(), g->d.dz, tab.data());
         g->zrow_max = z_row_abs_max(tab.data(), d->nz, d->r_z);
-        std::vector<float> tf(tab.begin(), tab.end());
+        // one row per plane, copied whole into the sweep's shared memory: each
+        // weight twice (an f32x2 operand), then the plane's damping factor
+        const int zr = vti_zrow(d->r_z);
+        std::vector<float> tf((size_t)d->nz * zr, 0.0f);
+        for (int k = 0; k < d->nz; ++k) {
+            float *row = tf.data() + (size_t)k * zr;
+            for (int m = 0; m < nw; ++m) row[2 * m] = row[2 * m + 1] = (float)tab[(size_t)k * nw + m];
+            row[2 * nw] = (float)cerjan(k, d->nz, d->sponge_width, d->sponge_a);
+        }
         rc = upload(reinterpret_cast<void **>(&g->ztab), tf.data(), tf.size() * sizeof(float), g->stream);
         if (rc) return bail(rc);
     }

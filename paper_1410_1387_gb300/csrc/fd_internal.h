@@ -56,6 +56,8 @@ struct alignas(16) IsoArgs {
     float w0;               // centre weight c0 (2/h^2 + 1/dz^2)
     float wxy[kMaxR + 1];   // c_l / h^2
     float wz[kMaxR + 1];    // c_l / dz^2
+    float2 wxy2[kMaxR + 1]; // (c_l / h^2, c_l / h^2): operands of packed f32x2 FMAs
+    float2 wz2[kMaxR + 1];
     Source src;
     RecLattice rec;
     RecLattice inj;         // additive sources on a lattice: row n - t0 of inj.trace at step n
@@ -69,12 +71,13 @@ struct VtiArgs {
     const float *p, *q;     // p^n, q^n
     const float *kx, *kn, *kz;
     const float *gx, *gy, *gz;
-    const float *ztab;      // nz x (2 R_z + 1) z weights (dz absorbed)
+    const float *ztab;      // nz rows of vti_zrow(R_z) floats: paired z weights, then G_z(k)
     long long pitch, plane;
     int nx, ny, nz;
     int zchunk;
     float w0;               // 2 c0 / h^2
     float wxy[kMaxR + 1];   // c_l / h^2
+    float2 wxy2[kMaxR + 1]; // (c_l / h^2, c_l / h^2) for packed f32x2 FMAs
     Source src;
     RecLattice rec;
     DevState *st;
@@ -131,6 +134,10 @@ struct alignas(128) BatchShot {
 };
 cudaError_t launch_iso_batch(int R, const Launch &L, const int4 *items, int nitems, const BatchShot *shots,
                              int max_zchunk, cudaStream_t s);
+
+// Floats per plane row of the VTI z table: the 2 R_z + 1 weights each twice,
+// then the plane's damping factor, padded to 16 bytes.
+constexpr int vti_zrow(int rz) { return (2 * (2 * rz + 1) + 1 + 3) / 4 * 4; }
 
 // Tensor maps of one VTI launch: p^n with the R_xy halo, tiles of q^n, p_prev,
 // q_prev and the three kappa arrays.

@@ -168,6 +168,8 @@ extern "C" int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u
     for (int l = 1; l <= R; ++l) {
         a.wxy[l] = (float)(c[l] / h2);
         a.wz[l] = (float)(c[l] / dz2);
+        a.wxy2[l] = make_float2(a.wxy[l], a.wxy[l]);
+        a.wz2[l] = make_float2(a.wz[l], a.wz[l]);
     }
     // the kernel reads sample tab[time index]; the status block's index is 0
     a.src = Source{reinterpret_cast<const float *>(scr + kOffSrc), has_src ? 1 : 0, has_src ? src_ix : -1,

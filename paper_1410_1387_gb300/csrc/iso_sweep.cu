@@ -244,6 +244,10 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 const float4 v = *reinterpret_cast<const float4 *>(rw + 4 * m);
                 xw[4 * m + 0] = v.x; xw[4 * m + 1] = v.y; xw[4 * m + 2] = v.z; xw[4 * m + 3] = v.w;
             }
+            // One accumulator per point, terms in a fixed order (centre, x pairs,
+            // y pairs, z pairs).  The y and z sums use packed f32x2 FMA / add on
+            // the point pairs (0, 1) and (2, 3): per lane the same rounding as
+            // fmaf, with half the instructions.
             float acc[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[e] = a.w0 * xw[R + e];
@@ -251,14 +255,13 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             for (int l = 1; l <= R; ++l)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[e] = fmaf(a.wxy[l], xw[R + e + l] + xw[R + e - l], acc[e]);
+            float2 lo = make_float2(acc[0], acc[1]), hi = make_float2(acc[2], acc[3]);
 #pragma unroll
             for (int l = 1; l <= R; ++l) {
                 const float4 up = *reinterpret_cast<const float4 *>(t + own + l * C::SW);
                 const float4 dn = *reinterpret_cast<const float4 *>(t + own - l * C::SW);
-                acc[0] = fmaf(a.wxy[l], up.x + dn.x, acc[0]);
-                acc[1] = fmaf(a.wxy[l], up.y + dn.y, acc[1]);
-                acc[2] = fmaf(a.wxy[l], up.z + dn.z, acc[2]);
-                acc[3] = fmaf(a.wxy[l], up.w + dn.w, acc[3]);
+                lo = __ffma2_rn(a.wxy2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo);
+                hi = __ffma2_rn(a.wxy2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi);
             }
             // this warp no longer reads plane k from either ring
             __syncwarp();
@@ -268,11 +271,15 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             }
 #pragma unroll
             for (int l = 1; l <= R; ++l) {
-                acc[0] = fmaf(a.wz[l], q[R + l].x + q[R - l].x, acc[0]);
-                acc[1] = fmaf(a.wz[l], q[R + l].y + q[R - l].y, acc[1]);
-                acc[2] = fmaf(a.wz[l], q[R + l].z + q[R - l].z, acc[2]);
-                acc[3] = fmaf(a.wz[l], q[R + l].w + q[R - l].w, acc[3]);
+                lo = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(q[R + l].x, q[R + l].y),
+                                                     make_float2(q[R - l].x, q[R - l].y)), lo);
+                hi = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(q[R + l].z, q[R + l].w),
+                                                     make_float2(q[R - l].z, q[R - l].w)), hi);
             }
+            acc[0] = lo.x;
+            acc[1] = lo.y;
+            acc[2] = hi.x;
+            acc[3] = hi.y;
 
             if (act) {
                 const float gyz = gyv * gz;

@@ -32,7 +32,9 @@ struct VtiCfg {
     static constexpr int SH = TY + 2 * RXY;
     static constexpr int SLOT_A = SW * SH;
     static constexpr int TILE = TX * TY;
-    static constexpr int SLOT_B = 6 * TILE;         // p_prev, q_prev, kx, kn, kz, q ahead
+    static constexpr int ZROW = vti_zrow(RZ);       // paired z weights and G_z of the plane
+    // p_prev, q_prev, kx, kn, kz, q ahead, then the z row (slots stay 128-byte aligned)
+    static constexpr int SLOT_B = 6 * TILE + (ZROW + 31) / 32 * 32;
     static constexpr int NA = LA + 1;
     static constexpr int NB = LA + 1;
     static constexpr int OFF_B = NA * SLOT_A * 4;
@@ -117,8 +119,9 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
                     break;
                 }
                 const bool ahead = k + RZ < a.nz;
-                mbar_arrive_expect_tx(&fullB[sb], (ahead ? 6 : 5) * C::TILE * 4);
+                mbar_arrive_expect_tx(&fullB[sb], (ahead ? 6 : 5) * C::TILE * 4 + C::ZROW * 4);
                 float *dst = ringB + sb * C::SLOT_B;
+                bulk_load(dst + 6 * C::TILE, a.ztab + (long long)k * C::ZROW, C::ZROW * 4, &fullB[sb]);
                 tma_load_3d(dst + 0 * C::TILE, &tm_pp, &fullB[sb], x0, y0, k);
                 tma_load_3d(dst + 1 * C::TILE, &tm_qp, &fullB[sb], x0, y0, k);
                 tma_load_3d(dst + 2 * C::TILE, &tm_kx, &fullB[sb], x0, y0, k);
@@ -178,6 +181,17 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             const float4 kzv = *reinterpret_cast<const float4 *>(tb + 4 * C::TILE);
             qq[2 * RZ] = (k + RZ < a.nz) ? *reinterpret_cast<const float4 *>(tb + 5 * C::TILE) : zero4;
 
+            // Dq from the plane's z row (weights paired for f32x2), l = -RZ..RZ ascending
+            const float *zrow = ringB + sb * C::SLOT_B + 6 * C::TILE;
+            float2 dq_lo = make_float2(0.f, 0.f), dq_hi = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m < C::NW; ++m) {
+                const float2 w2 = *reinterpret_cast<const float2 *>(zrow + 2 * m);
+                dq_lo = __ffma2_rn(w2, make_float2(qq[m].x, qq[m].y), dq_lo);
+                dq_hi = __ffma2_rn(w2, make_float2(qq[m].z, qq[m].w), dq_hi);
+            }
+            const float gz = zrow[2 * C::NW];
+
             if (!mbar_wait_bounded(&fullA[sa], (u / C::NA) & 1, kVtiWaitLimit)) {
                 ok = false;
                 break;
@@ -201,35 +215,28 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
                     for (int e = 0; e < 4; ++e) hp[e] = fmaf(a.wxy[l], xw[RXY + e + l] + xw[RXY + e - l], hp[e]);
             }
             const float4 pc = *reinterpret_cast<const float4 *>(t + own);
+            // y pairs with packed f32x2 on points (0, 1) and (2, 3)
+            float2 hp_lo = make_float2(hp[0], hp[1]), hp_hi = make_float2(hp[2], hp[3]);
 #pragma unroll
             for (int l = 1; l <= RXY; ++l) {
                 const float4 up = *reinterpret_cast<const float4 *>(t + own + l * C::SW);
                 const float4 dn = *reinterpret_cast<const float4 *>(t + own - l * C::SW);
-                hp[0] = fmaf(a.wxy[l], up.x + dn.x, hp[0]);
-                hp[1] = fmaf(a.wxy[l], up.y + dn.y, hp[1]);
-                hp[2] = fmaf(a.wxy[l], up.z + dn.z, hp[2]);
-                hp[3] = fmaf(a.wxy[l], up.w + dn.w, hp[3]);
+                hp_lo = __ffma2_rn(a.wxy2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), hp_lo);
+                hp_hi = __ffma2_rn(a.wxy2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hp_hi);
             }
+            hp[0] = hp_lo.x;
+            hp[1] = hp_lo.y;
+            hp[2] = hp_hi.x;
+            hp[3] = hp_hi.y;
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&emptyA[sa]);
                 mbar_arrive(&emptyB[sb]);
             }
-
-            // Dq: weights of plane k, l = -RZ..RZ in ascending order
-            float dq[4] = {0.f, 0.f, 0.f, 0.f};
-            const float *wr = a.ztab + (long long)k * C::NW;
-#pragma unroll
-            for (int m = 0; m < C::NW; ++m) {
-                const float w = __ldg(wr + m);
-                dq[0] = fmaf(w, qq[m].x, dq[0]);
-                dq[1] = fmaf(w, qq[m].y, dq[1]);
-                dq[2] = fmaf(w, qq[m].z, dq[2]);
-                dq[3] = fmaf(w, qq[m].w, dq[3]);
-            }
+            const float dq[4] = {dq_lo.x, dq_lo.y, dq_hi.x, dq_hi.y};
 
             if (act) {
-                const float gyz = gyv * a.gz[k];
+                const float gyz = gyv * gz;
                 const float pcu[4] = {pc.x, pc.y, pc.z, pc.w};
                 const float qc[4] = {qq[RZ].x, qq[RZ].y, qq[RZ].z, qq[RZ].w};
                 const float ppu[4] = {ppv.x, ppv.y, ppv.z, ppv.w};
