@@ -218,6 +218,35 @@ int fd_destroy_grid(fd_grid_t *g);
 /* Copy the calling thread's last error message into buf (always terminated). */
 int fd_last_error(char *buf, size_t n);
 
+/* ---- z slabs of one shot ------------------------------------------------------
+ * One grid (Sec. 1) cut along z into slabs, each a grid of its own (all on one
+ * GPU, or one per GPU), stored with P >= R ghost planes (VTI: R_z) on every
+ * side that has a neighbour: slab s owns planes [a_s, b_s) and stores
+ * [a_s - P, b_s + P) clipped to the column.  A step only reads points within R
+ * of the point it updates, so after every step it suffices to replace the
+ * ghost planes of the new level by the neighbours' planes there; the interior
+ * of every slab then holds, bit for bit, the values of the unsplit grid.  The
+ * source and the receivers go to the slab that owns their plane (local
+ * indices).  An extension for shots larger than one GPU: the paper runs one
+ * grid per device.
+ */
+
+/* Declare that local plane k of g is plane kg0 + k of a column of nz_global
+   planes, so that the damping layer along z follows the column rather than
+   the slab.  Uniform dz only (FD_ERR_UNSUPPORTED when the grid has dz_k).
+   Invalidates g's step graphs; call it before g joins a batch. */
+int fd_set_z_window(fd_grid_t *g, int kg0, int nz_global);
+
+/* Ghost-plane exchange between the z-neighbours `lower` and `upper` on one
+   device: copies the current level (ISO: u; VTI: p and q) of lower's planes
+   [nz_l - 2P, nz_l - P) to upper's [0, P) and upper's [P, 2P) to lower's
+   [nz_l - P, nz_l), P = planes.  Requires P >= the z radius, z windows that
+   overlap by 2P planes (upper's kg0 = lower's kg0 + nz_l - 2P), equal mode,
+   radii, nx, ny and time index, and one stream for both grids (the copies are
+   asynchronous on it).  Across GPUs the same planes travel point to point
+   between ranks instead. */
+int fd_halo_exchange(fd_grid_t *lower, fd_grid_t *upper, int planes);
+
 /* ---- adjoint and velocity gradient -----------------------------------------
  * For J = 1/2 sum_n sum_r (u^{n+1}(x_r) - dobs[n][r])^2 of an isotropic run
  * (an extension: the paper computes no gradients; its use is imaging).  The

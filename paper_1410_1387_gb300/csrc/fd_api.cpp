@@ -111,6 +111,8 @@ struct fd_grid {
     DevState *st_host = nullptr; // pinned copy
     float *gx = nullptr, *gy = nullptr, *gz = nullptr;
     float *ztab = nullptr;
+    std::vector<float> zrows;    // host copy of ztab (VTI)
+    int kg0 = 0, nzg = 0;        // local plane k is plane kg0 + k of a column of nzg planes
     double zrow_max = 0.0;       // Gershgorin bound of the z operator (VTI)
     double sig_xy = 0.0;         // Gershgorin bound of the 1D x-y operator (unit grid)
     float w0 = 0.f, wxy[kMaxR + 1] = {}, wz[kMaxR + 1] = {};
@@ -295,6 +297,20 @@ int upload(void **dst, const void *src, size_t bytes, cudaStream_t s)
     return FD_OK;
 }
 
+// Damping factors along z of the local planes (the planes kg0.. of a column
+// of nzg planes), and for VTI the z rows that end with the same factor.
+int upload_z_tables(fd_grid *g)
+{
+    const fd_desc &d = g->d;
+    std::vector<float> pz(d.nz);
+    for (int k = 0; k < d.nz; ++k) pz[k] = (float)cerjan(g->kg0 + k, g->nzg, d.sponge_width, d.sponge_a);
+    int rc = upload(reinterpret_cast<void **>(&g->gz), pz.data(), pz.size() * 4, g->stream);
+    if (rc || d.mode != FD_MODE_VTI) return rc;
+    const int zr = vti_zrow(d.r_z), nw = 2 * d.r_z + 1;
+    for (int k = 0; k < d.nz; ++k) g->zrows[(size_t)k * zr + 2 * nw] = pz[k];
+    return upload(reinterpret_cast<void **>(&g->ztab), g->zrows.data(), g->zrows.size() * 4, g->stream);
+}
+
 // A receiver set that is a row-major lattice on one z plane with constant
 // strides: fills the geometry of L (not its buffer, origin step or capacity).
 bool detect_lattice(const int *idx, int nrec, RecLattice *L)
@@ -471,25 +487,24 @@ int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stre
         g->zrow_max = z_row_abs_max(tab.data(), d->nz, d->r_z);
         // one row per plane, copied whole into the sweep's shared memory: each
         // weight twice (an f32x2 operand), then the plane's damping factor
+        // (filled in by upload_z_tables)
         const int zr = vti_zrow(d->r_z);
-        std::vector<float> tf((size_t)d->nz * zr, 0.0f);
+        g->zrows.assign((size_t)d->nz * zr, 0.0f);
         for (int k = 0; k < d->nz; ++k) {
-            float *row = tf.data() + (size_t)k * zr;
+            float *row = g->zrows.data() + (size_t)k * zr;
             for (int m = 0; m < nw; ++m) row[2 * m] = row[2 * m + 1] = (float)tab[(size_t)k * nw + m];
-            row[2 * nw] = (float)cerjan(k, d->nz, d->sponge_width, d->sponge_a);
         }
-        rc = upload(reinterpret_cast<void **>(&g->ztab), tf.data(), tf.size() * sizeof(float), g->stream);
-        if (rc) return bail(rc);
     }
     // damping profiles (Cerjan), padded to the pitch for 128-bit loads
-    std::vector<float> px(lay.pitch, 1.0f), py(d->ny), pz(d->nz);
+    std::vector<float> px(lay.pitch, 1.0f), py(d->ny);
     for (int i = 0; i < d->nx; ++i) px[i] = (float)cerjan(i, d->nx, d->sponge_width, d->sponge_a);
     for (int j = 0; j < d->ny; ++j) py[j] = (float)cerjan(j, d->ny, d->sponge_width, d->sponge_a);
-    for (int k = 0; k < d->nz; ++k) pz[k] = (float)cerjan(k, d->nz, d->sponge_width, d->sponge_a);
     if ((rc = upload(reinterpret_cast<void **>(&g->gx), px.data(), px.size() * 4, g->stream)) ||
-        (rc = upload(reinterpret_cast<void **>(&g->gy), py.data(), py.size() * 4, g->stream)) ||
-        (rc = upload(reinterpret_cast<void **>(&g->gz), pz.data(), pz.size() * 4, g->stream)))
+        (rc = upload(reinterpret_cast<void **>(&g->gy), py.data(), py.size() * 4, g->stream)))
         return bail(rc);
+    g->kg0 = 0;
+    g->nzg = d->nz;
+    if ((rc = upload_z_tables(g))) return bail(rc);
 
     rc = set_launch(g, default_launch(d));
     if (rc) return bail(rc);
@@ -812,6 +827,50 @@ int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch)
     const int b[4] = {g->cur, 1 - g->cur, 2 + g->cur, 3 - g->cur};
     *dev_ptr = g->field[b[which]];
     if (pitch) *pitch = g->lay.pitch;
+    return FD_OK;
+}
+
+int fd_set_z_window(fd_grid_t *g, int kg0, int nz_global)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (kg0 < 0 || nz_global < 1 || (long long)kg0 + g->d.nz > nz_global)
+        return fail(FD_ERR_INVALID_ARG, "planes [%d, %d) do not lie in a column of %d planes", kg0, kg0 + g->d.nz,
+                    nz_global);
+    if (!g->dzk.empty()) return fail(FD_ERR_UNSUPPORTED, "z windows need a uniform dz");
+    g->kg0 = kg0;
+    g->nzg = nz_global;
+    drop_graphs(g);   // the tables move
+    return upload_z_tables(g);
+}
+
+int fd_halo_exchange(fd_grid_t *lo, fd_grid_t *up, int planes)
+{
+    if (!lo || !up || lo == up) return fail(FD_ERR_INVALID_ARG, "need two distinct grids");
+    const fd_desc &a = lo->d, &b = up->d;
+    if (a.mode != b.mode || a.nx != b.nx || a.ny != b.ny || a.r_xy != b.r_xy || a.r_z != b.r_z)
+        return fail(FD_ERR_INVALID_ARG, "slabs differ in mode, radius or x-y size");
+    if (lo->dev != up->dev || lo->stream != up->stream)
+        return fail(FD_ERR_INVALID_ARG, "slabs must share a device and a stream");
+    const int rz = a.mode == FD_MODE_ISO ? a.r_xy : a.r_z;
+    if (planes < rz) return fail(FD_ERR_INVALID_ARG, "%d ghost planes, the z stencil needs %d", planes, rz);
+    if (a.nz < 2 * planes || b.nz < 2 * planes)
+        return fail(FD_ERR_INVALID_ARG, "slabs of %d and %d planes cannot hold %d ghost planes", a.nz, b.nz, planes);
+    if (lo->nzg != up->nzg || up->kg0 != lo->kg0 + a.nz - 2 * planes)
+        return fail(FD_ERR_INVALID_ARG, "z windows [%d, %d) and [%d, %d) do not overlap by %d planes", lo->kg0,
+                    lo->kg0 + a.nz, up->kg0, up->kg0 + b.nz, 2 * planes);
+    if (lo->n != up->n) return fail(FD_ERR_BAD_STATE, "slabs at time indices %d and %d", lo->n, up->n);
+    const size_t plane = (size_t)lo->lay.pitch * a.ny;
+    const size_t bytes = plane * planes * sizeof(float);
+    // current level: u (ISO), p and q (VTI)
+    const int nf = a.mode == FD_MODE_ISO ? 1 : 2;
+    for (int f = 0; f < nf; ++f) {
+        float *fl = lo->field[2 * f + lo->cur], *fu = up->field[2 * f + up->cur];
+        CU(cudaMemcpyAsync(fu, fl + (a.nz - 2 * planes) * plane, bytes, cudaMemcpyDeviceToDevice, lo->stream),
+           "ghost planes up");
+        CU(cudaMemcpyAsync(fl + (a.nz - planes) * plane, fu + planes * plane, bytes, cudaMemcpyDeviceToDevice,
+                           lo->stream),
+           "ghost planes down");
+    }
     return FD_OK;
 }
 

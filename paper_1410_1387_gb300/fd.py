@@ -41,6 +41,7 @@ EXPORTS = [
     "fd_batch_create", "fd_batch_set_launch", "fd_batch_set_graph", "fd_batch_add", "fd_batch_remove",
     "fd_batch_steps_left", "fd_batch_run", "fd_batch_destroy",
     "fd_set_injection", "fd_adjoint_source", "fd_grad_accumulate",
+    "fd_set_z_window", "fd_halo_exchange",
 ]
 
 
@@ -116,6 +117,8 @@ def lib() -> ctypes.CDLL:
             "fd_set_injection": [_vp, _vp, _i, _vp, _i],
             "fd_adjoint_source": [_vp, _vp, _vp, _i, _vp, ctypes.POINTER(ctypes.c_double)],
             "fd_grad_accumulate": [_vp, _vp, _vp, _vp],
+            "fd_set_z_window": [_vp, _i, _i],
+            "fd_halo_exchange": [_vp, _vp, _i],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -278,6 +281,14 @@ def fd_adjoint_source(g, traces, dobs, nt, inj) -> float:
 
 def fd_grad_accumulate(g, z, a, grad) -> None:
     _check(lib().fd_grad_accumulate(g, _ptr(z), _ptr(a), _ptr(grad)))
+
+
+def fd_set_z_window(g, kg0: int, nz_global: int) -> None:
+    _check(lib().fd_set_z_window(g, kg0, nz_global))
+
+
+def fd_halo_exchange(lower, upper, planes: int) -> None:
+    _check(lib().fd_halo_exchange(lower, upper, planes))
 
 
 def fd_batch_create(stream: int) -> int:
