@@ -121,6 +121,21 @@ def test_graph_and_tiles_are_bitwise_identical(fd):
     np.testing.assert_array_equal(t0, t2)
 
 
+@pytest.mark.parametrize("launch", [(64, 8, 17, 3), (32, 16, 9, 2)])
+def test_radius8_tiles_are_bitwise_identical(fd, O, launch):
+    """Radius 8 in other tiles, z chunks and lookaheads, ragged in x, y and z:
+    the same values bit for bit, and the oracle's within tolerance."""
+    rec = synth.receiver_plane(102, 70, 20, stride=3)
+    shot = iso_shot(102, 70, 58, 8, 20, seed=17, nb=8, receivers=rec)
+    (u0, p0), t0 = _run_gpu(fd, shot, 20)
+    (u1, p1), t1 = _run_gpu(fd, shot, 20, set_launch=launch)
+    np.testing.assert_array_equal(u0, u1)
+    np.testing.assert_array_equal(p0, p1)
+    np.testing.assert_array_equal(t0, t1)
+    u_ref, _, tr_ref = oracle_problem(O, shot).iso_run(shot.v, 20)
+    assert max_rel(u1, u_ref) <= 1e-4 and max_rel(t1, tr_ref) <= 1e-4
+
+
 def test_checkpoint_resume_is_bitwise(fd):
     shot = iso_shot(60, 50, 40, 4, 40, seed=13, nb=6)
     (u_full, p_full), tr_full = _run_gpu(fd, shot, 40)
