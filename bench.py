@@ -72,6 +72,13 @@ def make_shot(wl: str, n: int, seed: int, with_model=True):
     return synth.vti_shot(n, nsteps=1000, seed=seed, with_model=with_model)
 
 
+def l2_note(read_bytes: int) -> str:
+    """How the timed steps relate to the 129 MB L2 (no flush between steps)."""
+    if read_bytes > 129e6:
+        return f"no flush: every step reads {read_bytes / 2**30:.2f} GiB of inputs (> 129 MB L2)"
+    return f"inputs of {read_bytes / 1e6:.0f} MB per step may stay in the 129 MB L2 (small diagnostic size)"
+
+
 def workload_config(wl, shot, args):
     w = WORKLOADS[wl]
     return {
@@ -83,7 +90,7 @@ def workload_config(wl, shot, args):
         "damping_layer_cells": shot.nb,
         "receivers": int(len(shot.receivers)),
         "model": "10-layer velocity 1500-4500 m/s, +-5% cell noise, seeded",
-        "l2": "no flush: every step reads >= 1.5 GiB of inputs (> 129 MB L2)",
+        "l2": l2_note((3 if w["mode"] == "iso" else 7) * 4 * shot.nx * shot.ny * shot.nz),
         "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU",
     }
 
@@ -95,7 +102,8 @@ def workload_config(wl, shot, args):
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem,"
+              "temperature.gpu,temperature.memory")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -110,6 +118,12 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
+            # Start timing only once nvidia-smi samples: its start-up (NVML
+            # initialisation) slows the GPU for a moment, which would otherwise
+            # fall into the timed region.
+            t_end = time.time() + 5.0
+            while time.time() < t_end and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
             time.sleep(0.3)
         except Exception:
             self.proc = None
@@ -131,10 +145,10 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
+            if len(p) < 12:
                 continue
             try:
-                rows.append((float(p[1]), float(p[2]), float(p[3]), p[4], p[5:9]))
+                rows.append((float(p[1]), float(p[2]), float(p[3]), p[4], p[5:9], p[9:12]))
             except ValueError:
                 continue
         if not rows:
@@ -142,8 +156,14 @@ class ClockSampler:
         sm = [r[0] for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[4]) if v.lower() == "active"})
+        def num(i):
+            v = [float(r[5][i]) for r in rows if r[5][i].replace(".", "", 1).isdigit()]
+            return v
+        mem, tg, tm = num(0), num(1), num(2)
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
-                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons,
+                "mem_mhz": float(np.median(mem)) if mem else None,
+                "gpu_temp_c_max": max(tg) if tg else None, "mem_temp_c_max": max(tm) if tm else None}
 
 
 # ---------------------------------------------------------------------------
