@@ -925,6 +925,11 @@ struct fd_batch {
     int graph_steps = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // radius-8 members run on a stream of their own, forked from and joined
+    // back into the batch stream around every run, so the two kernels of a
+    // step overlap (each fills the other's last partial wave)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -1013,16 +1018,36 @@ int batch_rebuild(fd_batch *b)
     return FD_OK;
 }
 
-cudaError_t batch_enqueue_step(fd_batch *b, cudaStream_t s)
+// `steps` batch steps on stream s; radius-8 members on b->side when both radii
+// are present (forked from s after everything already on s, joined back).
+cudaError_t batch_enqueue_steps(fd_batch *b, int steps, cudaStream_t s)
 {
     const int radii[2] = {4, 8};
-    for (int r = 0; r < 2; ++r) {
-        if (!b->nitems[r]) continue;
-        cudaError_t e = launch_iso_batch(radii[r], b->L[r], b->d_items + b->off[r], b->nitems[r], b->d_shots,
-                                         b->max_zc[r], s);
-        if (e != cudaSuccess) return e;
+    const bool split = b->nitems[0] && b->nitems[1];
+    cudaError_t e = cudaSuccess;
+    if (split) {
+        if (!b->side) {
+            if ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(b->side, b->ev_fork, 0)) != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {
+        if (!b->nitems[r]) continue;
+        cudaStream_t sr = (split && r == 1) ? b->side : s;
+        for (int j = 0; j < steps && e == cudaSuccess; ++j)
+            e = launch_iso_batch(radii[r], b->L[r], b->d_items + b->off[r], b->nitems[r], b->d_shots,
+                                 b->max_zc[r], sr);
+    }
+    if (split) {
+        // join even after a failed launch, so that no capture is left forked
+        cudaError_t e1 = cudaEventRecord(b->ev_join, b->side);
+        cudaError_t e2 = cudaStreamWaitEvent(s, b->ev_join, 0);
+        if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    return e;
 }
 
 }  // namespace
@@ -1128,8 +1153,7 @@ int fd_batch_run(fd_batch_t *b, int max_steps, int *steps_run)
         if (!b->gexec) {
             if (!b->cap_stream) CU(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream create");
             CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            cudaError_t e = cudaSuccess;
-            for (int j = 0; j < K && e == cudaSuccess; ++j) e = batch_enqueue_step(b, b->cap_stream);
+            cudaError_t e = batch_enqueue_steps(b, K, b->cap_stream);
             cudaGraph_t graph = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
             if (e != cudaSuccess) {
@@ -1147,8 +1171,8 @@ int fd_batch_run(fd_batch_t *b, int max_steps, int *steps_run)
         CU(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
         left -= K;
     }
-    for (; left > 0; --left) {
-        cudaError_t e = batch_enqueue_step(b, b->stream);
+    if (left > 0) {
+        cudaError_t e = batch_enqueue_steps(b, left, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     }
     for (auto &m : b->members) {
@@ -1166,6 +1190,12 @@ int fd_batch_destroy(fd_batch_t *b)
     cudaStreamSynchronize(b->stream);
     batch_drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->side) {
+        cudaStreamSynchronize(b->side);
+        cudaStreamDestroy(b->side);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->d_shots) cudaFree(b->d_shots);
     if (b->d_items) cudaFree(b->d_items);
     delete b;

@@ -53,6 +53,12 @@ def test_batch_graph_and_tiles(fdm):
     tr2 = batch.run_batched(shots, graph_steps=3, launch={4: (32, 16, 20, 3)})[0]
     tr3 = batch.run_batched(shots, launch={4: (128, 8, 0, 3)})[0]
     assert batch.traces_equal(tr0, tr1) and batch.traces_equal(tr0, tr2) and batch.traces_equal(tr0, tr3)
+    # both radii: the radius-8 members run on a forked stream, inside graphs too
+    mixed = small_survey(radii=(4, 8), count=5, seed=14)
+    assert len({s.r_xy for s in mixed}) == 2
+    tm0 = batch.run_per_shot(mixed)[0]
+    tm1 = batch.run_batched(mixed, graph_steps=4)[0]
+    assert batch.traces_equal(tm0, tm1)
 
 
 def test_batch_against_oracle(fdm, O):
