@@ -1,0 +1,33 @@
+"""bench.py's reference arm (the FP64 oracle timed on the host cores) keeps
+the JSON contract on CPU: one line with the metric, unit, value, the oracle's
+core count and sample, and an end-to-end entry with no host-device bytes."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "24",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "grid-point updates/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["config"]["grid"] == [24, 24, 24] and d["config"]["workload"] == "iso512_r4_layered"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0 and e["value"] == d["value"]
+
+
+def test_l2_note_tracks_the_input_size():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.l2_note(3 * 4 * 512 ** 3).startswith("no flush")
+    assert "may stay" in bench.l2_note(3 * 4 * 64 ** 3)
