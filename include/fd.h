@@ -132,6 +132,31 @@ int fd_set_model(fd_grid_t *g, const float *vz, const float *eps, const float *d
                  int ptr_kind);
 
 /*
+ * Stencil weights.  By default a grid uses the maximal-order (Taylor) weights
+ * of Eq. 4, c_l = 2 (-1)^{l+1} (R!)^2 / (l^2 (R-l)! (R+l)!), c_0 = -2 sum c_l,
+ * and the per-plane Eq. 5 weights in z.  Sec. 1 notes that the weights can be
+ * optimised instead (after Holberg 1987; the paper gives no method or values).
+ *
+ * fd_optimized_weights writes radius + 1 band-optimised weights c_0..c_R of
+ * the unit-grid second derivative (the stencil c_0 u_0 + sum c_l (u_l + u_-l)):
+ * exact on quadratics (sum l^2 c_l = 1, c_0 = -2 sum c_l) and, among those,
+ * the least-squares minimum of the relative symbol error
+ *   int_0^kmax (4 sum_l c_l sin^2(l k / 2) / k^2 - 1)^2 dk,
+ * so the numerical phase velocity stays closest to the true one for
+ * wavenumbers k h <= kmax.  1 <= radius <= 12, 0 < kmax <= pi.  Pure host call.
+ *
+ * fd_set_weights installs unit-grid weights (radius + 1 doubles, in units of
+ * 1/h^2 and 1/dz^2) for the x-y stencil and, with a uniform dz, the z stencil;
+ * NULL keeps the current ones.  They must be exact on constants and quadratics
+ * (FD_ERR_INVALID_ARG otherwise); z weights on a grid with dz_k return
+ * FD_ERR_UNSUPPORTED.  Call it before fd_set_model (FD_ERR_BAD_STATE after),
+ * whose stability check uses the installed weights; fd_stability_limit()
+ * assumes the default ones.
+ */
+int fd_optimized_weights(int radius, double kmax, double *weights);
+int fd_set_weights(fd_grid_t *g, const double *w_xy, const double *w_z);
+
+/*
  * Ricker point source (Sec. 1) at cell (ix, iy, iz): step n adds
  *   dt^2 * amp * s(n dt - t0) / V,  s(t) = (1 - 2 pi^2 f^2 t^2) exp(-pi^2 f^2 t^2),
  * to the new level of p (ISO: u), and of q too when inject_q != 0 (VTI only).

@@ -194,7 +194,25 @@ typedef struct {
     double src_volume;    /* cell volume dividing the point source */
     int nrec;             /* receivers */
     const int *rec;       /* 3*nrec cell indices (ix, iy, iz) */
+    const double *cxy;    /* optional r_xy+1 unit-grid weights c_0..c_R along x and y (NULL: Taylor) */
+    const double *cz;     /* optional r_z+1 unit-grid weights along z for a uniform dz (NULL: Taylor) */
 } or_cfg;
+
+/* The weights a run uses: the caller's (cxy, cz) where given, else Taylor's. */
+static int stencil_weights(const or_cfg *c, double *cw, double *cz)
+{
+    if (c->cxy) {
+        for (int l = 0; l <= c->r_xy; ++l) cw[l] = c->cxy[l];
+    } else if (or_taylor_weights(c->r_xy, cw)) {
+        return -1;
+    }
+    if (c->cz) {
+        for (int l = 0; l <= c->r_z; ++l) cz[l] = c->cz[l];
+    } else if (or_taylor_weights(c->r_z, cz)) {
+        return -1;
+    }
+    return 0;
+}
 
 static inline double at(const double *u, const or_cfg *c, int i, int j, int k)
 {
@@ -235,7 +253,7 @@ static double op_z(const or_cfg *c, const double *cz, const double *u, int i, in
 int or_iso_laplacian(const or_cfg *c, const double *u, double *Lu)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
@@ -248,7 +266,7 @@ int or_iso_laplacian(const or_cfg *c, const double *u, double *Lu)
 int or_vti_operators(const or_cfg *c, const double *p, const double *q, double *Hp, double *Dq)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
@@ -288,7 +306,7 @@ int or_iso_run(const or_cfg *c, const double *v, double *u, double *uprev,
                int n0, int nsteps, double *traces)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
     size_t N = (size_t)c->nx * (size_t)c->ny * (size_t)c->nz;
     double *un = (double *)malloc(sizeof(double) * (N ? N : 1));
     double *cur = (double *)malloc(sizeof(double) * (N ? N : 1));
@@ -344,7 +362,7 @@ int or_vti_run(const or_cfg *c, const double *vz, const double *eps, const doubl
                int n0, int nsteps, double *traces)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
     size_t N = (size_t)c->nx * (size_t)c->ny * (size_t)c->nz;
     size_t B = sizeof(double) * (N ? N : 1);
     double *pn = malloc(B), *pc = malloc(B), *pp = malloc(B);
@@ -420,7 +438,7 @@ int or_iso_step_points(const or_cfg *c, const float *v, const float *u,
                        int npts, const int *pts, const double *uprev_pts, int n, double *out)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
 #pragma omp parallel for schedule(static)
     for (int m = 0; m < npts; ++m) {
         int i = pts[3 * m], j = pts[3 * m + 1], k = pts[3 * m + 2];
@@ -451,7 +469,7 @@ int or_vti_step_points(const or_cfg *c, const float *vz, const float *eps, const
                        double *outp, double *outq)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
     int nw = 2 * c->r_z + 1;
 #pragma omp parallel for schedule(static)
     for (int m = 0; m < npts; ++m) {
@@ -508,7 +526,7 @@ int or_iso_misfit_grad(const or_cfg *c, const double *v, const double *dobs, int
                        double *grad_v)
 {
     double cw[33], cz[33];
-    if (or_taylor_weights(c->r_xy, cw) || or_taylor_weights(c->r_z, cz)) return -1;
+    if (stencil_weights(c, cw, cz)) return -1;
     const size_t N = (size_t)c->nx * (size_t)c->ny * (size_t)c->nz;
     const size_t B = sizeof(double) * (N ? N : 1);
     double *U = (double *)calloc((size_t)(nsteps + 1) * (N ? N : 1), sizeof(double));   /* u^0..u^N */

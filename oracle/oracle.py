@@ -46,6 +46,7 @@ class Cfg(ctypes.Structure):
         ("src_f", ctypes.c_double), ("src_t0", ctypes.c_double), ("src_amp", ctypes.c_double),
         ("src_into_q", ctypes.c_int), ("src_volume", ctypes.c_double),
         ("nrec", ctypes.c_int), ("rec", ctypes.POINTER(ctypes.c_int)),
+        ("cxy", ctypes.POINTER(ctypes.c_double)), ("cz", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -106,6 +107,56 @@ def taylor_weights(R: int) -> np.ndarray:
     return c
 
 
+def symbol_ratio(c, k):
+    """-S(k) / k^2 of the unit-grid stencil c (S(k) = c_0 + 2 sum c_l cos(l k)),
+    1 for the exact second derivative; its k -> 0 limit is sum_l l^2 c_l."""
+    c = np.asarray(c, dtype=np.float64)
+    k = np.atleast_1d(np.asarray(k, dtype=np.float64))
+    out = np.empty_like(k)
+    small = np.abs(k) < 1e-6
+    l = np.arange(1, len(c))
+    kk = k[~small][:, None]
+    out[~small] = (4.0 * np.sin(0.5 * l * kk) ** 2 / kk ** 2) @ c[1:]
+    out[small] = (l ** 2) @ c[1:]
+    return out
+
+
+def optimized_weights(R: int, kmax: float, samples: int = 4001) -> np.ndarray:
+    """Band-optimised second-derivative weights (Sec. 1 notes that the weights
+    can be optimised, after Holberg 1987; it gives no method).  Read here as:
+    c_0..c_R exact on constants and quadratics (c_0 = -2 sum c_l,
+    sum l^2 c_l = 1) minimising int_0^kmax (-S(k)/k^2 - 1)^2 dk, the squared
+    relative error of the numerical phase velocity squared.  Solved as a
+    linear least-squares problem in c_2..c_R (c_1 from the quadratic
+    constraint) on `samples` equispaced wavenumbers with Simpson weights."""
+    if R < 1 or not (0.0 < kmax <= np.pi):
+        raise ValueError("radius >= 1 and 0 < kmax <= pi")
+    c = np.zeros(R + 1)
+    if R == 1:
+        c[:] = [-2.0, 1.0]
+        return c
+    n = samples if samples % 2 == 1 else samples + 1
+    k = np.linspace(0.0, kmax, n)
+    w = np.ones(n)
+    w[1:-1:2], w[2:-1:2] = 4.0, 2.0
+    w *= (k[1] - k[0]) / 3.0
+    # phi_l(k) = -S_l(k) / k^2 of the unit stencil "c_l = 1": 4 sin^2(l k/2) / k^2
+    phi = np.empty((n, R))
+    for l in range(1, R + 1):
+        e = np.zeros(R + 1)
+        e[l] = 1.0
+        phi[:, l - 1] = symbol_ratio(e, k)
+    ls = np.arange(2, R + 1)
+    A = phi[:, 1:] - phi[:, [0]] * (ls ** 2)[None, :]
+    b = 1.0 - phi[:, 0]
+    sw = np.sqrt(w)[:, None]
+    x = np.linalg.lstsq(A * sw, b * sw[:, 0], rcond=None)[0]
+    c[2:] = x
+    c[1] = 1.0 - (ls ** 2) @ x
+    c[0] = -2.0 * c[1:].sum()
+    return c
+
+
 def lagrange_d2(z, k: int) -> np.ndarray:
     """Second-derivative weights at node z[k] from all nodes z (Eq. 5)."""
     z = _c64(z)
@@ -155,7 +206,7 @@ class Problem:
 
     def __init__(self, nx, ny, nz, *, r_xy, r_z=None, h, dz=None, dzk=None, dt,
                  nb=0, sponge_a=0.0, src=None, src_f=15.0, src_t0=None, src_amp=1.0,
-                 src_into_q=False, src_volume=None, receivers=None):
+                 src_into_q=False, src_volume=None, receivers=None, weights_xy=None, weights_z=None):
         r_z = r_xy if r_z is None else r_z
         dz = h if dz is None else dz
         self.shape = (nz, ny, nx)
@@ -190,6 +241,15 @@ class Problem:
             c.src_volume = src_volume
         c.nrec = len(self.rec)
         c.rec = self.rec.ctypes.data_as(_I) if len(self.rec) else None
+        # optional stencil weights (default: Taylor, Eq. 4); z weights need a uniform dz
+        self.wxy = None if weights_xy is None else _c64(weights_xy)
+        self.wz = None if weights_z is None else _c64(weights_z)
+        if self.wxy is not None:
+            assert self.wxy.shape == (r_xy + 1,)
+            c.cxy = _dp(self.wxy)
+        if self.wz is not None:
+            assert self.wz.shape == (r_z + 1,) and dzk is None
+            c.cz = _dp(self.wz)
         self.cfg = c
 
     @property

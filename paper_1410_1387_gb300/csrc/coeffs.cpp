@@ -53,6 +53,99 @@ void central_d2(int R, double *c)
     for (int l = 1; l <= R; ++l) c[l] = 0.5 * (w[R + l] + w[R - l]);
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton's iteration on P_n from
+// the first guess cos(pi (i + 3/4) / (n + 1/2)), P_n by the three-term recurrence.
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double step = p1 / dp;
+            t -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+int band_optimized_d2(int R, double kmax, double *c)
+{
+    if (R < 1 || R > 32 || !(kmax > 0.0) || kmax > M_PI) return -1;
+    if (R == 1) {
+        c[0] = -2.0;
+        c[1] = 1.0;
+        return 0;
+    }
+    // relative symbol error e(k) = sum_l c_l phi_l(k) - 1, phi_l = 4 sin^2(l k / 2) / k^2
+    // (phi_l(0) = l^2); with c_1 = 1 - sum_{l>=2} l^2 c_l the constraint e(0) = 0
+    // holds and e = sum_{l>=2} c_l (phi_l - l^2 phi_1) - (1 - phi_1): a linear least-
+    // squares problem in c_2..c_R, sampled at composite Gauss-Legendre points.
+    constexpr int NQ = 16, NS = 32;
+    double gx[NQ], gw[NQ];
+    gauss_legendre(NQ, gx, gw);
+    const int M = NQ * NS, P = R - 1;
+    std::vector<double> A((size_t)M * P), b(M);
+    auto phi = [](int l, double k) {
+        const double s = std::sin(0.5 * l * k);
+        return 4.0 * s * s / (k * k);
+    };
+    for (int si = 0; si < NS; ++si)
+        for (int q = 0; q < NQ; ++q) {
+            const int row = si * NQ + q;
+            const double k = (si + 0.5 * (gx[q] + 1.0)) * kmax / NS;
+            const double sw = std::sqrt(0.5 * gw[q] * kmax / NS);
+            const double p1 = phi(1, k);
+            for (int l = 2; l <= R; ++l) A[(size_t)row * P + (l - 2)] = sw * (phi(l, k) - l * l * p1);
+            b[row] = sw * (1.0 - p1);
+        }
+    // Householder QR of A, applied to b as it goes; then back substitution
+    for (int j = 0; j < P; ++j) {
+        double nrm = 0.0;
+        for (int i = j; i < M; ++i) nrm += A[(size_t)i * P + j] * A[(size_t)i * P + j];
+        nrm = std::sqrt(nrm);
+        if (nrm == 0.0) return -1;
+        const double a0 = A[(size_t)j * P + j];
+        const double alpha = a0 > 0.0 ? -nrm : nrm;
+        std::vector<double> v(M - j);
+        v[0] = a0 - alpha;
+        for (int i = j + 1; i < M; ++i) v[i - j] = A[(size_t)i * P + j];
+        double vv = 0.0;
+        for (double e : v) vv += e * e;
+        if (vv == 0.0) continue;
+        for (int col = j; col <= P; ++col) {   // col == P is b
+            double dot = 0.0;
+            for (int i = j; i < M; ++i) dot += v[i - j] * (col < P ? A[(size_t)i * P + col] : b[i]);
+            const double f = 2.0 * dot / vv;
+            for (int i = j; i < M; ++i) (col < P ? A[(size_t)i * P + col] : b[i]) -= f * v[i - j];
+        }
+    }
+    std::vector<double> xs(P);
+    for (int j = P - 1; j >= 0; --j) {
+        double s = b[j];
+        for (int m = j + 1; m < P; ++m) s -= A[(size_t)j * P + m] * xs[m];
+        xs[j] = s / A[(size_t)j * P + j];
+    }
+    double c1 = 1.0, sum = 0.0;
+    for (int l = 2; l <= R; ++l) {
+        c[l] = xs[l - 2];
+        c1 -= (double)l * l * c[l];
+        sum += c[l];
+    }
+    c[1] = c1;
+    c[0] = -2.0 * (sum + c1);
+    for (int l = 0; l <= R; ++l)
+        if (!std::isfinite(c[l])) return -1;
+    return 0;
+}
+
 double row_abs_sum(const double *c, int R)
 {
     double s = std::fabs(c[0]);

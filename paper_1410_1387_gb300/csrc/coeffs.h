@@ -7,6 +7,13 @@ namespace fdk {
 void fornberg(double x0, const double *x, int n, int M, double *out);
 // Symmetric order-2R second-derivative weights c[0..R] on a unit grid (Eq. 4).
 void central_d2(int R, double *c);
+// Band-optimised symmetric second-derivative weights c[0..R] on a unit grid:
+// exact on quadratics (sum_l l^2 c_l = 1, c_0 = -2 sum c_l) and, within that,
+// least-squares optimal for the relative error of the symbol,
+// int_0^kmax (-S(k) / k^2 - 1)^2 dk with S(k) = c_0 + 2 sum_l c_l cos(l k)
+// (the optimised weights of Sec. 1, after Holberg 1987).  0 < kmax <= pi.
+// Returns 0, or -1 for bad arguments.
+int band_optimized_d2(int R, double kmax, double *c);
 // |c_0| + 2 sum |c_l|: the Gershgorin bound of the 1D operator's spectrum
 // (equal to its symbol at the Nyquist frequency for the alternating Taylor weights).
 double row_abs_sum(const double *c, int R);

@@ -112,6 +112,10 @@ struct fd_grid {
     float *gx = nullptr, *gy = nullptr, *gz = nullptr;
     float *ztab = nullptr;
     std::vector<float> zrows;    // host copy of ztab (VTI)
+    double cxy[kMaxR + 1] = {};  // unit-grid second-derivative weights along x and y (Eq. 4)
+    double cz[kMaxR + 1] = {};   // along z when dz is uniform (Eq. 4; VTI: replaces Eq. 5's rows)
+    bool custom_z = false;       // VTI: z rows from cz rather than from the plane spacings
+    double sig_z = 0.0;          // Gershgorin bound of the 1D z operator (isotropic, unit grid)
     int kg0 = 0, nzg = 0;        // local plane k is plane kg0 + k of a column of nzg planes
     double zrow_max = 0.0;       // Gershgorin bound of the z operator (VTI)
     double sig_xy = 0.0;         // Gershgorin bound of the 1D x-y operator (unit grid)
@@ -297,6 +301,49 @@ int upload(void **dst, const void *src, size_t bytes, cudaStream_t s)
     return FD_OK;
 }
 
+// Single-precision weights of the sweeps, their Gershgorin bounds and (VTI)
+// the z rows, from the unit-grid weights cxy and cz.
+int apply_weights(fd_grid *g)
+{
+    const fd_desc &d = g->d;
+    const double h2 = d.h * d.h;
+    g->sig_xy = row_abs_sum(g->cxy, d.r_xy);
+    for (int l = 0; l <= kMaxR; ++l) {
+        g->wxy[l] = (l >= 1 && l <= d.r_xy) ? (float)(g->cxy[l] / h2) : 0.0f;
+        g->wz[l] = 0.0f;
+    }
+    if (d.mode == FD_MODE_ISO) {
+        const double dz2 = d.dz * d.dz;
+        bool same = true;
+        for (int l = 0; l <= d.r_xy; ++l) same = same && g->cxy[l] == g->cz[l];
+        g->w0 = same ? (float)(g->cxy[0] * (2.0 / h2 + 1.0 / dz2)) : (float)(2.0 * g->cxy[0] / h2 + g->cz[0] / dz2);
+        for (int l = 1; l <= d.r_z; ++l) g->wz[l] = (float)(g->cz[l] / dz2);
+        g->sig_z = row_abs_sum(g->cz, d.r_z);
+        return FD_OK;
+    }
+    g->w0 = (float)(2.0 * g->cxy[0] / h2);
+    const int nw = 2 * d.r_z + 1;
+    std::vector<double> tab((size_t)d.nz * nw);
+    if (g->custom_z) {
+        const double dz2 = d.dz * d.dz;
+        for (int k = 0; k < d.nz; ++k)
+            for (int l = -d.r_z; l <= d.r_z; ++l) tab[(size_t)k * nw + l + d.r_z] = g->cz[l < 0 ? -l : l] / dz2;
+    } else {
+        z_weights(d.nz, d.r_z, g->dzk.empty() ? nullptr : g->dzk.data(), d.dz, tab.data());
+    }
+    g->zrow_max = z_row_abs_max(tab.data(), d.nz, d.r_z);
+    // one row per plane, copied whole into the sweep's shared memory: each
+    // weight twice (an f32x2 operand), then the plane's damping factor
+    // (filled in by upload_z_tables)
+    const int zr = vti_zrow(d.r_z);
+    g->zrows.assign((size_t)d.nz * zr, 0.0f);
+    for (int k = 0; k < d.nz; ++k) {
+        float *row = g->zrows.data() + (size_t)k * zr;
+        for (int m = 0; m < nw; ++m) row[2 * m] = row[2 * m + 1] = (float)tab[(size_t)k * nw + m];
+    }
+    return FD_OK;
+}
+
 // Damping factors along z of the local planes (the planes kg0.. of a column
 // of nzg planes), and for VTI the z rows that end with the same factor.
 int upload_z_tables(fd_grid *g)
@@ -470,31 +517,9 @@ int fd_create_grid(const fd_desc *d, void *arena, size_t arena_bytes, void *stre
     if (e != cudaSuccess) return bail(cuda_fail(e, "wavefield clear"));
 
     // weights (Eq. 4 on x-y; Eq. 4 on z for the isotropic case, Eq. 5 for VTI)
-    double c[kMaxR + 1];
-    central_d2(d->r_xy, c);
-    g->sig_xy = row_abs_sum(c, d->r_xy);
-    const double h2 = d->h * d->h;
-    for (int l = 1; l <= d->r_xy; ++l) g->wxy[l] = (float)(c[l] / h2);
-    if (d->mode == FD_MODE_ISO) {
-        const double dz2 = d->dz * d->dz;
-        g->w0 = (float)(c[0] * (2.0 / h2 + 1.0 / dz2));
-        for (int l = 1; l <= d->r_z; ++l) g->wz[l] = (float)(c[l] / dz2);
-    } else {
-        g->w0 = (float)(2.0 * c[0] / h2);
-        const int nw = 2 * d->r_z + 1;
-        std::vector<double> tab((size_t)d->nz * nw);
-        z_weights(d->nz, d->r_z, g->dzk.empty() ? nullptr : g->dzk.data(), g->d.dz, tab.data());
-        g->zrow_max = z_row_abs_max(tab.data(), d->nz, d->r_z);
-        // one row per plane, copied whole into the sweep's shared memory: each
-        // weight twice (an f32x2 operand), then the plane's damping factor
-        // (filled in by upload_z_tables)
-        const int zr = vti_zrow(d->r_z);
-        g->zrows.assign((size_t)d->nz * zr, 0.0f);
-        for (int k = 0; k < d->nz; ++k) {
-            float *row = g->zrows.data() + (size_t)k * zr;
-            for (int m = 0; m < nw; ++m) row[2 * m] = row[2 * m + 1] = (float)tab[(size_t)k * nw + m];
-        }
-    }
+    central_d2(d->r_xy, g->cxy);
+    central_d2(d->r_z, g->cz);
+    if ((rc = apply_weights(g))) return bail(rc);
     // damping profiles (Cerjan), padded to the pitch for 128-bit loads
     std::vector<float> px(lay.pitch, 1.0f), py(d->ny);
     for (int i = 0; i < d->nx; ++i) px[i] = (float)cerjan(i, d->nx, d->sponge_width, d->sponge_a);
@@ -569,7 +594,7 @@ int fd_set_model(fd_grid_t *g, const float *vz, const float *eps, const float *d
     double lam;
     if (!vti) {
         const double dz2 = d.dz * d.dz;
-        lam = kmax * (2.0 * g->sig_xy / (d.h * d.h) + g->sig_xy / dz2);
+        lam = kmax * (2.0 * g->sig_xy / (d.h * d.h) + g->sig_z / dz2);
     } else {
         lam = (double)s.kxmax * 2.0 * g->sig_xy / (d.h * d.h) + kmax * g->zrow_max;
     }
@@ -828,6 +853,48 @@ int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch)
     *dev_ptr = g->field[b[which]];
     if (pitch) *pitch = g->lay.pitch;
     return FD_OK;
+}
+
+int fd_optimized_weights(int radius, double kmax, double *weights)
+{
+    if (!weights) return fail(FD_ERR_INVALID_ARG, "weights is NULL");
+    if (radius < 1 || radius > kMaxR) return fail(FD_ERR_INVALID_ARG, "radius %d outside 1..%d", radius, kMaxR);
+    if (!(kmax > 0.0) || kmax > M_PI) return fail(FD_ERR_INVALID_ARG, "kmax %g outside (0, pi]", kmax);
+    if (band_optimized_d2(radius, kmax, weights)) return fail(FD_ERR_INVALID_ARG, "weight fit failed");
+    return FD_OK;
+}
+
+int fd_set_weights(fd_grid_t *g, const double *w_xy, const double *w_z)
+{
+    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (g->model_set) return fail(FD_ERR_BAD_STATE, "set the weights before the model (the stability check uses them)");
+    const fd_desc &d = g->d;
+    // a second-derivative stencil: exact on constants and on x^2 / 2
+    auto consistent = [](const double *w, int R) {
+        double s = w[0], a = std::fabs(w[0]), q = 0.0;
+        for (int l = 1; l <= R; ++l) {
+            if (!std::isfinite(w[l])) return false;
+            s += 2.0 * w[l];
+            a += 2.0 * std::fabs(w[l]);
+            q += (double)l * l * w[l];
+        }
+        return std::isfinite(w[0]) && std::fabs(s) <= 1e-9 * a && std::fabs(q - 1.0) <= 1e-6;
+    };
+    if (w_xy && !consistent(w_xy, d.r_xy))
+        return fail(FD_ERR_INVALID_ARG, "x-y weights are not a consistent second derivative");
+    if (w_z) {
+        if (!g->dzk.empty()) return fail(FD_ERR_UNSUPPORTED, "z weights need a uniform dz");
+        if (!consistent(w_z, d.r_z)) return fail(FD_ERR_INVALID_ARG, "z weights are not a consistent second derivative");
+    }
+    if (w_xy) std::memcpy(g->cxy, w_xy, sizeof(double) * (d.r_xy + 1));
+    if (w_z) {
+        std::memcpy(g->cz, w_z, sizeof(double) * (d.r_z + 1));
+        if (d.mode == FD_MODE_VTI) g->custom_z = true;
+    }
+    drop_graphs(g);
+    int rc = apply_weights(g);
+    if (rc) return rc;
+    return (d.mode == FD_MODE_VTI && w_z) ? upload_z_tables(g) : FD_OK;
 }
 
 int fd_set_z_window(fd_grid_t *g, int kg0, int nz_global)

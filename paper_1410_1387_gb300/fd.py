@@ -41,7 +41,7 @@ EXPORTS = [
     "fd_batch_create", "fd_batch_set_launch", "fd_batch_set_graph", "fd_batch_add", "fd_batch_remove",
     "fd_batch_steps_left", "fd_batch_run", "fd_batch_destroy",
     "fd_set_injection", "fd_adjoint_source", "fd_grad_accumulate",
-    "fd_set_z_window", "fd_halo_exchange",
+    "fd_set_z_window", "fd_halo_exchange", "fd_optimized_weights", "fd_set_weights",
 ]
 
 
@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
             "fd_grad_accumulate": [_vp, _vp, _vp, _vp],
             "fd_set_z_window": [_vp, _i, _i],
             "fd_halo_exchange": [_vp, _vp, _i],
+            "fd_optimized_weights": [_i, _d, _vp],
+            "fd_set_weights": [_vp, _vp, _vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -281,6 +283,19 @@ def fd_adjoint_source(g, traces, dobs, nt, inj) -> float:
 
 def fd_grad_accumulate(g, z, a, grad) -> None:
     _check(lib().fd_grad_accumulate(g, _ptr(z), _ptr(a), _ptr(grad)))
+
+
+def fd_optimized_weights(radius: int, kmax: float) -> np.ndarray:
+    """Band-optimised unit-grid second-derivative weights c_0..c_radius."""
+    out = np.zeros(radius + 1, dtype=np.float64)
+    _check(lib().fd_optimized_weights(radius, kmax, out.ctypes.data))
+    return out
+
+
+def fd_set_weights(g, w_xy=None, w_z=None) -> None:
+    a = None if w_xy is None else np.ascontiguousarray(w_xy, dtype=np.float64)
+    b = None if w_z is None else np.ascontiguousarray(w_z, dtype=np.float64)
+    _check(lib().fd_set_weights(g, _ptr(a), _ptr(b)))
 
 
 def fd_set_z_window(g, kg0: int, nz_global: int) -> None:

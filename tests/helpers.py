@@ -5,12 +5,12 @@ import numpy as np
 from paper_1410_1387_gb300 import synth
 
 
-def oracle_problem(O, shot, receivers=True):
+def oracle_problem(O, shot, receivers=True, **kw):
     return O.Problem(shot.nx, shot.ny, shot.nz, r_xy=shot.r_xy, r_z=shot.r_z, h=shot.h,
                      dz=shot.dz, dzk=shot.dzk, dt=shot.dt, nb=shot.nb,
                      sponge_a=shot.sponge_a if shot.nb else 0.0, src=shot.src, src_f=shot.src_f,
                      src_t0=shot.src_t0, src_amp=shot.src_amp, src_into_q=shot.src_into_q,
-                     receivers=shot.receivers if receivers else None)
+                     receivers=shot.receivers if receivers else None, **kw)
 
 
 def iso_shot(nx, ny, nz, R, nsteps, seed, nb=0, src=None, receivers=None, layered=True,

@@ -93,6 +93,22 @@ def test_invalid_descriptions(fd, kw, code):
     assert fd.fd_last_error()
 
 
+@pytest.mark.parametrize("R,kmax", [(1, 1.0), (4, 2.0), (8, 2.3), (12, 2.5), (4, 3.14159)])
+def test_optimized_weights_match_oracle(fd, O, R, kmax):
+    """The library's band-optimised weights (Gauss-Legendre quadrature, Householder
+    QR) against the oracle's (Simpson sampling, SVD least squares)."""
+    a = fd.fd_optimized_weights(R, kmax)
+    b = O.optimized_weights(R, kmax)
+    assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("R,kmax", [(0, 1.0), (13, 1.0), (4, 0.0), (4, 3.2), (4, float("nan"))])
+def test_optimized_weights_reject_bad_arguments(fd, R, kmax):
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_optimized_weights(max(R, 0), kmax)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+
+
 def test_no_fallback_when_library_missing(monkeypatch):
     from paper_1410_1387_gb300 import fd as fdmod
     monkeypatch.setattr(fdmod, "LIB_PATH", "/nonexistent/libfd.so")

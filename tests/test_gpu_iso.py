@@ -136,6 +136,58 @@ def test_radius8_tiles_are_bitwise_identical(fd, O, launch):
     assert max_rel(u1, u_ref) <= 1e-4 and max_rel(t1, tr_ref) <= 1e-4
 
 
+def _weighted_grid(fd, shot, w_xy, w_z):
+    g = fd.Grid(fd.GridSpec.from_shot(shot), device="cuda:0")
+    fd.fd_set_weights(g.h, w_xy, w_z)
+    if shot.mode == "vti":
+        g.set_model(shot.v, shot.eps, shot.delta)
+    else:
+        g.set_model(shot.v)
+    g.add_source(*shot.src, freq_hz=shot.src_f, t0=shot.src_t0, amp=shot.src_amp, inject_q=shot.src_into_q)
+    g.set_receivers(shot.receivers, shot.nsteps)
+    return g
+
+
+def test_optimized_weights_parity(fd, O):
+    """Band-optimised weights (Sec. 1; kmax = 2.0 on all axes) installed with
+    fd_set_weights: the GPU run matches the oracle run with the oracle's own
+    optimised weights, and differs from the Taylor run."""
+    shot = iso_shot(48, 40, 36, 4, 60, seed=23, nb=5, receivers=synth.receiver_plane(48, 40, 10, stride=2))
+    w = fd.fd_optimized_weights(4, 2.0)
+    g = _weighted_grid(fd, shot, w, w)
+    g.run(shot.nsteps)
+    u, _ = g.state()
+    tr = g.traces()
+    g.close()
+    wo = O.optimized_weights(4, 2.0)
+    ur, _, trr = oracle_problem(O, shot, weights_xy=wo, weights_z=wo).iso_run(shot.v, shot.nsteps)
+    assert max_rel(u, ur) <= 1e-4 and rel_l2(u, ur) <= 1e-4 and max_rel(tr, trr) <= 1e-4
+    (ut, _), _ = _run_gpu(fd, shot, shot.nsteps)
+    assert max_rel(ut, ur) > 1e-3
+
+
+def test_set_weights_errors(fd):
+    shot = iso_shot(20, 20, 20, 4, 5, seed=1)
+    g = fd.Grid(fd.GridSpec.from_shot(shot), device="cuda:0")
+    bad = fd.fd_optimized_weights(4, 2.0)
+    bad[2] *= 1.01                                   # no longer exact on quadratics
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_set_weights(g.h, bad, None)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+    g.set_model(shot.v)
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_set_weights(g.h, fd.fd_optimized_weights(4, 2.0), None)
+    assert e.value.code == fd.FD_ERR_BAD_STATE
+    g.close()
+    v = synth.vti_shot(24, nsteps=2)
+    gv = fd.Grid(fd.GridSpec.from_shot(v), device="cuda:0")
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_set_weights(gv.h, None, fd.fd_optimized_weights(8, 2.0))    # stretched dz
+    assert e.value.code == fd.FD_ERR_UNSUPPORTED
+    fd.fd_set_weights(gv.h, fd.fd_optimized_weights(12, 2.5), None)
+    gv.close()
+
+
 def test_checkpoint_resume_is_bitwise(fd):
     shot = iso_shot(60, 50, 40, 4, 40, seed=13, nb=6)
     (u_full, p_full), tr_full = _run_gpu(fd, shot, 40)

@@ -74,6 +74,23 @@ def test_vti_reduces_to_iso_on_gpu(fd):
     assert max_rel(tr, tri) <= 1e-5
 
 
+def test_vti_optimized_weights(fd, O):
+    """The paper's operator with band-optimised weights (R_xy = 12 at kmax 2.5,
+    R_z = 8 at kmax 2.3, uniform dz) against the oracle with its own optimised
+    weights."""
+    from tests.test_gpu_iso import _weighted_grid
+    shot = vti_small(40, 36, 32, 30, seed=6, nb=4)
+    shot.dzk, shot.dz = None, shot.h
+    g = _weighted_grid(fd, shot, fd.fd_optimized_weights(12, 2.5), fd.fd_optimized_weights(8, 2.3))
+    g.run(shot.nsteps)
+    p, _, q, _ = g.state()
+    tr = g.traces()
+    g.close()
+    P = oracle_problem(O, shot, weights_xy=O.optimized_weights(12, 2.5), weights_z=O.optimized_weights(8, 2.3))
+    pr, _, qr, _, trr = P.vti_run(shot.v, shot.eps, shot.delta, shot.nsteps)
+    assert max_rel(p, pr) <= 1e-4 and max_rel(q, qr) <= 1e-4 and max_rel(tr, trr) <= 1e-4
+
+
 def test_vti_rejects_eps_below_delta(fd):
     shot = vti_small(20, 20, 20, 5, seed=2)
     shot.delta[4, 5, 6] = shot.eps[4, 5, 6] + 0.01

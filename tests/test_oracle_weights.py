@@ -4,7 +4,12 @@
 * the Taylor moment conditions, solved exactly in rationals here (a different
   characterisation from the oracle's closed form),
 * the variable-spacing z weights: exactness on polynomials up to degree 2R_z on
-  stretched nodes, and reduction to the uniform weights on uniform nodes.
+  stretched nodes, and reduction to the uniform weights on uniform nodes,
+* the band-optimised weights (Sec. 1, after Holberg 1987): the two consistency
+  constraints, optimality of the band error computed by adaptive quadrature
+  (vanishing directional derivatives, and scipy's SLSQP reaching the same
+  weights from the Taylor start), the Taylor weights as the band shrinks
+  (quadratically), and a band error far below Taylor's.
 """
 import math
 import os
@@ -131,3 +136,76 @@ def test_z_table_rows(O):
     c = O.taylor_weights(Rz)
     np.testing.assert_allclose(tu, np.tile(np.concatenate([c[:0:-1], c]) / 100.0, (nz, 1)),
                                rtol=1e-9, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# band-optimised weights
+# ---------------------------------------------------------------------------
+
+def _band_error(O, c, kmax):
+    """int_0^kmax (-S(k)/k^2 - 1)^2 dk by adaptive quadrature (independent of
+    the oracle's Simpson sampling)."""
+    from scipy import integrate
+    return integrate.quad(lambda k: (O.symbol_ratio(c, k)[0] - 1.0) ** 2, 0.0, kmax, limit=400,
+                          epsabs=1e-18, epsrel=1e-12)[0]
+
+
+def _null_direction(R, rng):
+    """A weight perturbation that keeps both constraints (sum l^2 d_l = 0,
+    d_0 = -2 sum d_l)."""
+    d = np.zeros(R + 1)
+    d[1:] = rng.standard_normal(R)
+    l2 = np.arange(1, R + 1) ** 2
+    d[1:] -= (l2 @ d[1:]) / (l2 @ l2) * l2
+    d[0] = -2.0 * d[1:].sum()
+    return d
+
+
+@pytest.mark.parametrize("R,kmax", [(2, 1.5), (4, 2.0), (8, 2.3), (12, 2.5)])
+def test_optimized_weights_constraints(O, R, kmax):
+    c = O.optimized_weights(R, kmax)
+    assert abs(c[0] + 2.0 * c[1:].sum()) <= 1e-12 * np.abs(c).sum()
+    assert abs((np.arange(1, R + 1) ** 2) @ c[1:] - 1.0) <= 1e-12
+    assert abs(O.symbol_ratio(c, 0.0)[0] - 1.0) <= 1e-12
+
+
+@pytest.mark.parametrize("R,kmax", [(4, 2.0), (8, 2.3)])
+def test_optimized_weights_are_optimal(O, R, kmax):
+    c = O.optimized_weights(R, kmax)
+    e0 = _band_error(O, c, kmax)
+    rng = np.random.default_rng(R)
+    for _ in range(3):
+        d = _null_direction(R, rng)
+        h = 1e-3 * np.abs(c).max() / np.abs(d).max()
+        ep, em = _band_error(O, c + h * d, kmax), _band_error(O, c - h * d, kmax)
+        slope, curv = (ep - em) / (2 * h), (ep + em - 2 * e0) / h ** 2
+        assert curv > 0 and abs(slope) <= 1e-6 * curv * np.abs(c).max()
+
+
+def test_optimized_weights_match_slsqp(O):
+    from scipy import optimize
+    R, kmax = 4, 2.0
+    c = O.optimized_weights(R, kmax)
+    l2 = np.arange(1, R + 1) ** 2
+    res = optimize.minimize(lambda x: _band_error(O, np.concatenate([[-2.0 * x.sum()], x]), kmax),
+                            O.taylor_weights(R)[1:], method="SLSQP",
+                            constraints=[{"type": "eq", "fun": lambda x: l2 @ x - 1.0}],
+                            options={"ftol": 1e-16, "maxiter": 500})
+    assert res.success
+    assert np.abs(res.x - c[1:]).max() <= 1e-5 * np.abs(c).max()
+
+
+def test_optimized_weights_tend_to_taylor(O):
+    t = O.taylor_weights(4)
+    dev = [np.abs(O.optimized_weights(4, km) - t).max() / np.abs(t).max() for km in (1.0, 0.5, 0.25)]
+    assert dev[2] < 1e-3
+    # quadratic in the band edge: halving kmax divides the deviation by ~4
+    assert 3.5 < dev[0] / dev[1] < 4.5 and 3.5 < dev[1] / dev[2] < 4.5
+
+
+@pytest.mark.parametrize("R,kmax", [(4, 2.0), (12, 2.5)])
+def test_optimized_band_error_below_taylor(O, R, kmax):
+    c, t = O.optimized_weights(R, kmax), O.taylor_weights(R)
+    assert _band_error(O, c, kmax) < 0.05 * _band_error(O, t, kmax)
+    k = np.linspace(1e-4, kmax, 2000)
+    assert np.abs(O.symbol_ratio(c, k) - 1).max() < np.abs(O.symbol_ratio(t, k) - 1).max()
