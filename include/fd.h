@@ -297,7 +297,8 @@ int fd_adjoint_source(fd_grid_t *g, const float *traces, const float *dobs, int 
                       double *misfit);
 
 /* grad += 2 dt z (L a) / sqrt(K) over g's grid; z, a, grad are device arrays
-   in g's pitched layout (fd_layout).  Asynchronous on g's stream. */
+   in g's pitched layout (fd_layout), 16-byte aligned (FD_ERR_INVALID_ARG
+   otherwise).  Asynchronous on g's stream. */
 int fd_grad_accumulate(fd_grid_t *g, const float *z, const float *a, float *grad);
 
 /* ---- batched shots --------------------------------------------------------

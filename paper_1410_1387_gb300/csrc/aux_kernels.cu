@@ -125,38 +125,6 @@ __global__ void gather_kernel(const float *field, long long pitch, long long pla
     trace[(long long)row * nrec + r] = field[(long long)k * plane + (long long)j * pitch + i];
 }
 
-// Velocity-gradient term of one step of the adjoint: grad += 2 dt z (L a) / sqrt(kappa),
-// L the isotropic Laplacian of the forward step (zero outside the grid).
-template <int R>
-__global__ void grad_kernel(const IsoArgs w, double dt, const float *__restrict__ z, const float *__restrict__ av,
-                            float *__restrict__ grad)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= w.nx) return;
-    const long long p = (long long)k * w.plane + (long long)j * w.pitch + i;
-    float L = w.w0 * av[p];
-#pragma unroll
-    for (int l = 1; l <= R; ++l) {
-        const float xp = i + l < w.nx ? av[p + l] : 0.f, xm = i - l >= 0 ? av[p - l] : 0.f;
-        const float yp = j + l < w.ny ? av[p + l * w.pitch] : 0.f, ym = j - l >= 0 ? av[p - l * w.pitch] : 0.f;
-        const float zp = k + l < w.nz ? av[p + l * w.plane] : 0.f, zm = k - l >= 0 ? av[p - l * w.plane] : 0.f;
-        L = fmaf(w.wxy[l], xp + xm, L);
-        L = fmaf(w.wxy[l], yp + ym, L);
-        L = fmaf(w.wz[l], zp + zm, L);
-    }
-    grad[p] += (float)(2.0 * dt) * z[p] * L * rsqrtf(w.kappa[p]);
-}
-
-cudaError_t launch_grad(const IsoArgs &w, int R, double dt, const float *z, const float *av, float *grad,
-                        cudaStream_t s)
-{
-    dim3 grid((w.nx + 127) / 128, w.ny, w.nz);
-    if (R == 4) grad_kernel<4><<<grid, 128, 0, s>>>(w, dt, z, av, grad);
-    else if (R == 8) grad_kernel<8><<<grid, 128, 0, s>>>(w, dt, z, av, grad);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
 // Adjoint source rows and misfit: row m of inj = kappa(x_r) times the residual
 // of step nt-1-m (the adjoint runs backward in time).
 __global__ void adjoint_source_kernel(const RecLattice rec, const float *__restrict__ kappa, long long pitch,

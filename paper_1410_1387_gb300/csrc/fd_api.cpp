@@ -137,6 +137,13 @@ struct fd_grid {
     CUtensorMap tm_halo[2];      // u (p) buffers, box (tx + 2 r_xy) x (ty + 2 r_xy)
     CUtensorMap tm_tile[4];      // every wavefield buffer, box tx x ty
     CUtensorMap tm_model[3];     // every model buffer, box tx x ty
+    // tensor maps of caller fields for the gradient sweep, by address and box
+    struct CachedMap {
+        const float *p;
+        int bx, by;
+        CUtensorMap m;
+    };
+    std::vector<CachedMap> map_cache;
     // graphs
     int graph_steps = 0;
     cudaStream_t cap_stream = nullptr;
@@ -299,6 +306,25 @@ int upload(void **dst, const void *src, size_t bytes, cudaStream_t s)
     // pageable source: staged before the call returns, so `src` may go away
     CU(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s), "table upload");
     return FD_OK;
+}
+
+// Tensor map of a caller's field in the grid's pitched layout (box bx x by x 1),
+// encoded once per address and box: the gradient sweep is called every step
+// with the same few buffers.
+int cached_map(fd_grid *g, const float *p, int bx, int by, CUtensorMap *out)
+{
+    for (const auto &e : g->map_cache)
+        if (e.p == p && e.bx == bx && e.by == by) {
+            *out = e.m;
+            return 0;
+        }
+    fd_grid::CachedMap e{p, bx, by, {}};
+    const int r = encode_field_map(&e.m, p, g->d.nx, g->d.ny, g->d.nz, g->lay.pitch, bx, by);
+    if (r) return r;
+    if (g->map_cache.size() >= 256) g->map_cache.erase(g->map_cache.begin());
+    g->map_cache.push_back(e);
+    *out = e.m;
+    return 0;
 }
 
 // Single-precision weights of the sweeps, their Gershgorin bounds and (VTI)
@@ -725,9 +751,23 @@ int fd_grad_accumulate(fd_grid_t *g, const float *z, const float *a, float *grad
     if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "the adjoint is isotropic-only");
     if (!g->model_set) return fail(FD_ERR_BAD_STATE, "no model");
     if (!z || !a || !grad) return fail(FD_ERR_INVALID_ARG, "NULL field");
+    if ((reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(grad)) % 16)
+        return fail(FD_ERR_INVALID_ARG, "fields must be 16-byte aligned");
     if (g->d.ny > 65535 || g->d.nz > 65535) return fail(FD_ERR_UNSUPPORTED, "grid too large for the gradient kernel");
-    const IsoArgs w = iso_args(g);
-    cudaError_t e = launch_grad(w, g->d.r_xy, g->d.dt, z, a, grad, g->stream);
+    const fd_desc &d = g->d;
+    const int R = d.r_xy;
+    const Launch L = iso_grad_launch(R, d.nx, d.ny, d.nz);
+    IsoMaps maps;
+    CUtensorMap mg;
+    if (cached_map(g, a, L.tx + 2 * R, L.ty + 2 * R, &maps.cur) || cached_map(g, z, L.tx, L.ty, &maps.prev) ||
+        cached_map(g, g->model[0], L.tx, L.ty, &maps.kappa) || cached_map(g, grad, L.tx, L.ty, &mg))
+        return fail(FD_ERR_CUDA, "tensor map encoding failed");
+    IsoArgs w = iso_args(g);
+    w.prev = grad;
+    w.cur = a;
+    w.zchunk = L.zchunk;
+    w.c2dt = (float)(2.0 * d.dt);
+    cudaError_t e = launch_iso_grad(R, L, maps, mg, w, g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gradient kernel");
     return FD_OK;
 }

@@ -63,6 +63,7 @@ struct alignas(16) IsoArgs {
     RecLattice inj;         // additive sources on a lattice: row n - t0 of inj.trace at step n
     DevState *st;
     unsigned int ncta;
+    float c2dt;             // 2 dt: the gradient sweep's factor
 };
 
 // Arguments of the VTI sweep (Eqs. 1-2, 4-5).
@@ -160,9 +161,12 @@ cudaError_t launch_model_vti(const float *vz, const float *eps, const float *del
 cudaError_t launch_gather(const float *field, long long pitch, long long plane, const int *idx,
                           int nrec, float *trace, int t0, int cap, const DevState *st,
                           cudaStream_t s);
-// grad += 2 dt z (L a) / sqrt(kappa) over the grid (L with a's weights in `a`).
-cudaError_t launch_grad(const IsoArgs &w, int R, double dt, const float *z, const float *av, float *grad,
-                        cudaStream_t s);
+// Gradient sweep: a.prev = grad (in/out), a.cur = the forward level, a.c2dt = 2 dt;
+// tm.cur = that level with the R halo, tm.prev = z, tm.kappa = kappa, tm_grad =
+// grad (tile boxes of L).  grad += 2 dt z (L a) / sqrt(kappa).
+Launch iso_grad_launch(int R, int nx, int ny, int nz);
+cudaError_t launch_iso_grad(int R, const Launch &L, const IsoMaps &tm, const CUtensorMap &tm_grad, const IsoArgs &a,
+                            cudaStream_t s);
 // inj[m][r] = kappa(x_r) (tr - dobs)[nt-1-m][r] on the lattice `rec`; misfit += 1/2 sum (tr - dobs)^2.
 cudaError_t launch_adjoint_source(const RecLattice &rec, const float *kappa, long long pitch, long long plane,
                                   const float *tr, const float *dobs, int nt, float *inj, double *misfit,

@@ -31,7 +31,9 @@ namespace fdk {
 // ~1 s at the GB300's 2 GHz SM clock: far beyond any TMA latency.
 constexpr long long kWaitLimit = 2000000000LL;
 
-template <int R, int TX, int TY, int LA>
+// NBT: tiles per ring B slot (u^{n-1} and kappa; z, kappa and the gradient
+// for the gradient sweep).
+template <int R, int TX, int TY, int LA, int NBT = 2>
 struct IsoCfg {
     static constexpr int NTX = TX / 4;              // consumer threads per tile row
     static constexpr int NC = NTX * TY;             // consumer threads
@@ -40,7 +42,7 @@ struct IsoCfg {
     static constexpr int SW = TX + 2 * R;           // staged row width (floats)
     static constexpr int SH = TY + 2 * R;           // staged rows
     static constexpr int SLOT_A = SW * SH;          // floats per u^n plane
-    static constexpr int SLOT_B = 2 * TX * TY;      // floats per (u^{n-1}, kappa) plane
+    static constexpr int SLOT_B = NBT * TX * TY;    // floats per ring B plane
     static constexpr int NA = R + 1 + LA;           // ring A slots
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
@@ -80,13 +82,17 @@ __device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_
 
 // One CTA's work: tile (bx, by), z chunk bz, of the step u^n -> u^{n+1}.
 // INJ compiles in the injection lattice (adjoint runs only: the extra branch
-// in the store path costs about 6 % when present).
-template <int R, int TX, int TY, int LA, bool INJ>
+// in the store path costs about 6 % when present).  GRAD turns the sweep into
+// the adjoint's velocity-gradient term: `cur` is the forward level a = u^n,
+// ring B carries z (tm_prev), kappa and the gradient (tm_grad), and each point
+// gets grad += a.c2dt z (L a) / sqrt(kappa), written over the gradient (`prev`).
+template <int R, int TX, int TY, int LA, bool INJ, bool GRAD = false>
 __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtensorMap *tm_prev,
                                          const CUtensorMap *tm_kappa, const IsoArgs &a, float *prev,
-                                         const float *cur, const int n, const int bx, const int by, const int bz)
+                                         const float *cur, const int n, const int bx, const int by, const int bz,
+                                         const CUtensorMap *tm_grad = nullptr)
 {
-    using C = IsoCfg<R, TX, TY, LA>;
+    using C = IsoCfg<R, TX, TY, LA, GRAD ? 3 : 2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ringA = reinterpret_cast<float *>(smem_raw);
     float *ringB = reinterpret_cast<float *>(smem_raw + C::OFF_B);
@@ -151,6 +157,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 float *dst = ringB + s * C::SLOT_B;
                 tma_load_3d(dst, tm_prev, &fullB[s], x0, y0, k);
                 tma_load_3d(dst + TX * TY, tm_kappa, &fullB[s], x0, y0, k);
+                if (GRAD) tma_load_3d(dst + 2 * TX * TY, tm_grad, &fullB[s], x0, y0, k);
                 b_end = k + 1;
             };
             for (int p = z0; ok && p < min(z0 + R, zend); ++p) issue_a(p);
@@ -232,6 +239,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             const float *tb = ringB + sb * C::SLOT_B;
             const float4 pv = *reinterpret_cast<const float4 *>(tb + ownb);
             const float4 kv = *reinterpret_cast<const float4 *>(tb + TX * TY + ownb);
+            const float4 gv = GRAD ? *reinterpret_cast<const float4 *>(tb + 2 * TX * TY + ownb) : zero4;
             const float gz = sgz[k - z0];
 
             const int sa = (k - z0) % C::NA;
@@ -281,7 +289,20 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             acc[2] = hi.x;
             acc[3] = hi.y;
 
-            if (act) {
+            if (GRAD && act) {
+                // velocity-gradient term: pv holds z, kv kappa, gv the gradient
+                const float zu[4] = {pv.x, pv.y, pv.z, pv.w}, ku[4] = {kv.x, kv.y, kv.z, kv.w};
+                float o[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[e] += a.c2dt * zu[e] * acc[e] * rsqrtf(ku[e]);
+                float *dst = prev + k * a.plane + rowoff;
+                if (gxi + 3 < a.nx) {
+                    st_cs(dst, make_float4(o[0], o[1], o[2], o[3]));
+                } else {
+                    for (int e = 0; e < 4; ++e)
+                        if (gxi + e < a.nx) dst[e] = o[e];
+                }
+            } else if (act) {
                 const float gyz = gyv * gz;
                 const float cu[4] = {xw[R], xw[R + 1], xw[R + 2], xw[R + 3]};
                 const float pu[4] = {pv.x, pv.y, pv.z, pv.w};
@@ -451,6 +472,56 @@ static cudaError_t launch_b(const int4 *items, int nitems, const BatchShot *shot
     if (nitems <= 0) return cudaSuccess;
     iso_batch_kernel<R, TX, TY, LA><<<nitems, C::NT, smem, s>>>(items, shots);
     return cudaGetLastError();
+}
+
+// Velocity-gradient sweep of the adjoint (fd_grad_accumulate): the same
+// pipeline over a = u^n, with z, kappa and the gradient in ring B.  It does not
+// advance the grid's time index.
+template <int R, int TX, int TY, int LA>
+__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+    iso_grad_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_z,
+                    const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_grad,
+                    const __grid_constant__ IsoArgs a)
+{
+    iso_body<R, TX, TY, LA, false, true>(&tm_a, &tm_z, &tm_kappa, a, a.prev, a.cur, 0, blockIdx.x, blockIdx.y,
+                                         blockIdx.z, &tm_grad);
+}
+
+template <int R, int TX, int TY, int LA>
+static cudaError_t launch_g(const IsoMaps &tm, const CUtensorMap &tm_grad, const IsoArgs &a0, cudaStream_t s)
+{
+    using C = IsoCfg<R, TX, TY, LA, 3>;
+    constexpr int smem_max = C::SMEM + 4 * kMaxChunk;
+    static bool attr_set[64] = {};   // per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(iso_grad_kernel<R, TX, TY, LA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    IsoArgs a = a0;
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
+    a.ncta = grid.x * grid.y * grid.z;
+    const int smem = C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4);
+    iso_grad_kernel<R, TX, TY, LA><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, tm_grad, a);
+    return cudaGetLastError();
+}
+
+Launch iso_grad_launch(int R, int nx, int ny, int nz)
+{
+    Launch L = R == 4 ? Launch{64, 16, 0, 3} : Launch{64, 8, 0, 2};
+    L.zchunk = default_zchunk(L, nx, ny, nz);
+    return L;
+}
+
+cudaError_t launch_iso_grad(int R, const Launch &L, const IsoMaps &tm, const CUtensorMap &tm_grad, const IsoArgs &a,
+                            cudaStream_t s)
+{
+    if (R == 4 && L.tx == 64 && L.ty == 16 && L.lookahead == 3) return launch_g<4, 64, 16, 3>(tm, tm_grad, a, s);
+    if (R == 8 && L.tx == 64 && L.ty == 8 && L.lookahead == 2) return launch_g<8, 64, 8, 2>(tm, tm_grad, a, s);
+    return cudaErrorInvalidConfiguration;
 }
 
 // The (R, tile, lookahead) combinations built into the library.
