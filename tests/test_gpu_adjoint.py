@@ -22,9 +22,9 @@ def mods():
     return fd, adjoint
 
 
-def small_shot(n=(40, 36, 32), steps=90, seed=4, anomaly=False):
+def small_shot(n=(40, 36, 32), steps=90, seed=4, anomaly=False, R=4):
     nx, ny, nz = n
-    s = synth.layered_shot(max(n), 4, nsteps=steps, seed=seed, with_model=False)
+    s = synth.layered_shot(max(n), R, nsteps=steps, seed=seed, with_model=False)
     s.nx, s.ny, s.nz = nx, ny, nz
     s.nb = 5
     s.src = (nx // 2, ny // 2, 9)
@@ -81,12 +81,13 @@ def _data(fd, s_true):
     return tr
 
 
-def test_gradient_matches_oracle(mods, O):
+@pytest.mark.parametrize("R", [4, 8])
+def test_gradient_matches_oracle(mods, O, R):
     import torch
     fd, adjoint = mods
-    true = small_shot(anomaly=True)
+    true = small_shot(anomaly=True, R=R)
     dobs = _data(fd, true)
-    bg = small_shot()
+    bg = small_shot(R=R)
     solver = adjoint.AdjointSolver(bg, checkpoint_every=20)
     J, _ = solver.forward(torch.from_numpy(bg.v).cuda(), torch.from_numpy(dobs).cuda())
     g = solver.backward().cpu().numpy().astype(np.float64)
