@@ -63,7 +63,10 @@ class Batch:
 
 
 def run_batched(shots, device=None, graph_steps=0, launch=None, keep_grids=False):
-    """All shots as one batch until each has run its own step count.
+    """All shots as one batch until each has run its own step count.  The
+    batch runs until a member finishes (64 steps at least), and finished members
+    leave before the next run (their work items would otherwise still be
+    launched, only to find their shot done).
 
     Returns (traces per shot, seconds from the first launch to the last trace
     read, grids if keep_grids)."""
@@ -81,8 +84,15 @@ def run_batched(shots, device=None, graph_steps=0, launch=None, keep_grids=False
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ev0.record(b.stream)
-    while b.run(1 << 20):
-        pass
+    live = list(grids)
+    while live:
+        # at least 64 steps per run: each change of membership rebuilds the work
+        # list and re-captures the graph, so members that finish a little
+        # earlier idle until the run ends
+        b.run(max(64, min(b.steps_left(g) for g in live)))
+        for g in [g for g in live if b.steps_left(g) == 0]:
+            b.remove(g)
+            live.remove(g)
     ev1.record(b.stream)
     traces = [g.traces() if g.nrec else None for g in grids]
     el = time.perf_counter() - t0

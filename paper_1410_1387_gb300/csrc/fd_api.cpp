@@ -1037,6 +1037,14 @@ struct fd_batch {
     // step overlap (each fills the other's last partial wave)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pinned host staging of the table uploads (two, used in turn)
+    struct Staging {
+        void *host = nullptr;
+        size_t cap = 0;
+        cudaEvent_t done = nullptr;
+    };
+    Staging stage[2];
+    int next_stage = 0;
 };
 
 namespace {
@@ -1090,36 +1098,57 @@ int batch_rebuild(fd_batch *b)
     }
     const size_t nit = items[0].size() + items[1].size();
     if (nit > 0x7fffffff) return fail(FD_ERR_OUT_OF_RANGE, "batch has too many work items");
+    // device tables: stream-ordered (re)allocation, so that growing them neither
+    // synchronises the device nor frees a table a queued launch still reads
     if (ns > b->cap_shots) {
-        if (b->d_shots) cudaFree(b->d_shots);
+        if (b->d_shots) cudaFreeAsync(b->d_shots, b->stream);
         b->d_shots = nullptr;
         b->cap_shots = 0;
-        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_shots), ns * sizeof(BatchShot));
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&b->d_shots), ns * sizeof(BatchShot), b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch descriptor allocation");
         b->cap_shots = ns;
     }
     if (nit > b->cap_items) {
-        if (b->d_items) cudaFree(b->d_items);
+        if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
         b->d_items = nullptr;
         b->cap_items = 0;
-        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->d_items), std::max<size_t>(nit, 1) * sizeof(int4));
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&b->d_items), std::max<size_t>(nit, 1) * sizeof(int4),
+                                        b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch work-list allocation");
         b->cap_items = std::max<size_t>(nit, 1);
     }
-    if (ns) CU(cudaMemcpyAsync(b->d_shots, shots.data(), ns * sizeof(BatchShot), cudaMemcpyHostToDevice, b->stream),
+    // Uploads from pinned staging (a pageable source would make the host wait for
+    // the launches already queued), alternating between two buffers; a buffer is
+    // reused once its previous upload has run.
+    fd_batch::Staging &st = b->stage[b->next_stage];
+    b->next_stage ^= 1;
+    if (st.done) CU(cudaEventSynchronize(st.done), "staging reuse");
+    else CU(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming), "event create");
+    const size_t need = ns * sizeof(BatchShot) + nit * sizeof(int4);
+    if (need > st.cap) {
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.cap = 0;
+        CU(cudaMallocHost(&st.host, need), "staging allocation");
+        st.cap = need;
+    }
+    char *hp = static_cast<char *>(st.host);
+    if (ns) std::memcpy(hp, shots.data(), ns * sizeof(BatchShot));
+    int4 *hi = reinterpret_cast<int4 *>(hp + ns * sizeof(BatchShot));
+    if (!items[0].empty()) std::memcpy(hi, items[0].data(), items[0].size() * sizeof(int4));
+    if (!items[1].empty()) std::memcpy(hi + items[0].size(), items[1].data(), items[1].size() * sizeof(int4));
+    if (ns) CU(cudaMemcpyAsync(b->d_shots, hp, ns * sizeof(BatchShot), cudaMemcpyHostToDevice, b->stream),
                "batch descriptor upload");
+    if (nit) CU(cudaMemcpyAsync(b->d_items, hi, nit * sizeof(int4), cudaMemcpyHostToDevice, b->stream),
+                "batch work-list upload");
+    CU(cudaEventRecord(st.done, b->stream), "event record");
     b->off[0] = 0;
     b->nitems[0] = (int)items[0].size();
     b->off[1] = b->nitems[0];
     b->nitems[1] = (int)items[1].size();
-    for (int r = 0; r < 2; ++r)
-        if (b->nitems[r])
-            CU(cudaMemcpyAsync(b->d_items + b->off[r], items[r].data(), items[r].size() * sizeof(int4),
-                               cudaMemcpyHostToDevice, b->stream),
-               "batch work-list upload");
     // No synchronisation: the uploads are ordered on the batch stream after the
-    // launches that read the previous lists, and their pageable sources were
-    // staged before the copy calls returned.
+    // launches that read the previous lists (the radius-8 stream joins the batch
+    // stream at the end of every run).
     b->dirty = false;
     batch_drop_graph(b);
     return FD_OK;
@@ -1303,8 +1332,13 @@ int fd_batch_destroy(fd_batch_t *b)
     }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
-    if (b->d_shots) cudaFree(b->d_shots);
-    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_shots) cudaFreeAsync(b->d_shots, b->stream);
+    if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
+    cudaStreamSynchronize(b->stream);
+    for (auto &st : b->stage) {
+        if (st.done) cudaEventDestroy(st.done);
+        if (st.host) cudaFreeHost(st.host);
+    }
     delete b;
     cudaGetLastError();
     return FD_OK;
