@@ -19,9 +19,7 @@ struct DevState {
     float kxmax;
     unsigned int bad;       // count of invalid model values
     unsigned int eps_lt_delta;
-    unsigned int work;      // next work item of a persistent sweep (0 between launches)
-    unsigned int exited;    // CTAs of the current launch that have finished
-    int pad[6];
+    int pad[8];
 };
 static_assert(sizeof(DevState) == 64, "status block size");
 constexpr int kErrTmaTimeout = 1;
