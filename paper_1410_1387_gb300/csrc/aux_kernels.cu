@@ -3,6 +3,8 @@
 // sets that are not a lattice on one plane.
 #include <math.h>
 
+#include <algorithm>
+
 #include <cudaTypedefs.h>
 
 #include "fd_internal.h"
@@ -54,19 +56,21 @@ __device__ __forceinline__ unsigned warp_sum(unsigned v)
 // One block per (row j, plane k); threads stride over x.  `src_pitch` is nx for
 // dense input or the field pitch when the input was copied in place.
 __global__ void model_iso_kernel(const float *v, long long src_pitch, float *kappa, int nx,
-                                 int ny, long long pitch, double dt, DevState *st)
+                                 long long rows, long long pitch, double dt, DevState *st)
 {
-    const int j = blockIdx.x, k = blockIdx.y;
-    const float *vr = v + ((long long)k * ny + j) * src_pitch;
-    float *kr = kappa + ((long long)k * ny + j) * pitch;
     float vmax = 0.f;
     unsigned bad = 0;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const float vv = vr[i];
-        if (!(vv > 0.f) || !isfinite(vv)) ++bad;
-        else vmax = fmaxf(vmax, vv);
-        const double vd = (double)vv * dt;
-        kr[i] = (float)(vd * vd);
+    // a block per row (j, k), rows taken in turn: ny * nz may exceed any grid dimension
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const float *vr = v + row * src_pitch;
+        float *kr = kappa + row * pitch;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const float vv = vr[i];
+            if (!(vv > 0.f) || !isfinite(vv)) ++bad;
+            else vmax = fmaxf(vmax, vv);
+            const double vd = (double)vv * dt;
+            kr[i] = (float)(vd * vd);
+        }
     }
     vmax = warp_max(vmax);
     bad = warp_sum(bad);
@@ -78,13 +82,13 @@ __global__ void model_iso_kernel(const float *v, long long src_pitch, float *kap
 
 __global__ void model_vti_kernel(const float *vz, const float *eps, const float *delta,
                                  long long src_pitch, float *kx, float *kn, float *kz, int nx,
-                                 int ny, long long pitch, double dt, DevState *st)
+                                 long long rows, long long pitch, double dt, DevState *st)
 {
-    const int j = blockIdx.x, k = blockIdx.y;
-    const long long so = ((long long)k * ny + j) * src_pitch;
-    const long long dof = ((long long)k * ny + j) * pitch;
     float vmax = 0.f, kxmax = 0.f;
     unsigned bad = 0, eld = 0;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const long long so = row * src_pitch;
+    const long long dof = row * pitch;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const float v = vz[so + i], e = eps[so + i], d = delta[so + i];
         if (!(v > 0.f) || !isfinite(v) || !isfinite(e) || !isfinite(d) || !(1.0f + 2.0f * d > 0.f))
@@ -99,6 +103,7 @@ __global__ void model_vti_kernel(const float *vz, const float *eps, const float 
         kx[dof + i] = (float)kxd;
         kn[dof + i] = (float)(k2 * (1.0 + 2.0 * (double)d));
         if (isfinite(kxd)) kxmax = fmaxf(kxmax, (float)kxd);
+    }
     }
     vmax = warp_max(vmax);
     kxmax = warp_max(kxmax);
@@ -157,8 +162,9 @@ cudaError_t launch_adjoint_source(const RecLattice &rec, const float *kappa, lon
 cudaError_t launch_model_iso(const float *v, long long src_pitch, float *kappa, int nx, int ny,
                              int nz, long long pitch, double dt, DevState *st, cudaStream_t s)
 {
-    dim3 grid(ny, nz);
-    model_iso_kernel<<<grid, 128, 0, s>>>(v, src_pitch, kappa, nx, ny, pitch, dt, st);
+    const long long rows = (long long)ny * nz;
+    model_iso_kernel<<<(unsigned)std::min<long long>(rows, 1 << 16), 128, 0, s>>>(v, src_pitch, kappa, nx, rows,
+                                                                                   pitch, dt, st);
     return cudaGetLastError();
 }
 
@@ -166,9 +172,9 @@ cudaError_t launch_model_vti(const float *vz, const float *eps, const float *del
                              long long src_pitch, float *kx, float *kn, float *kz, int nx, int ny,
                              int nz, long long pitch, double dt, DevState *st, cudaStream_t s)
 {
-    dim3 grid(ny, nz);
-    model_vti_kernel<<<grid, 128, 0, s>>>(vz, eps, delta, src_pitch, kx, kn, kz, nx, ny, pitch, dt,
-                                          st);
+    const long long rows = (long long)ny * nz;
+    model_vti_kernel<<<(unsigned)std::min<long long>(rows, 1 << 16), 128, 0, s>>>(vz, eps, delta, src_pitch, kx, kn,
+                                                                                   kz, nx, rows, pitch, dt, st);
     return cudaGetLastError();
 }
 

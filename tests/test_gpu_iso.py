@@ -85,6 +85,37 @@ def test_parity_degenerate_grids(fd, O, R, shape):
     assert max_rel(tr, trr) <= 1e-4
 
 
+@pytest.mark.parametrize("shape", [(200003, 2, 3), (3, 70001, 2), (2, 3, 300001)])
+def test_extreme_aspect_ratios(fd, O, shape):
+    """Long thin grids: hundreds of thousands of points along one axis (tens of
+    thousands of tiles in x or y, z chunks capped at their maximum in z)."""
+    nx, ny, nz = shape
+    src = (nx // 2, ny // 2, nz // 2)
+    rec = np.array([[nx // 2 + 3 if nx > 10 else 0, ny // 2 + 3 if ny > 10 else 0,
+                     nz // 2 + 3 if nz > 10 else 0]], np.int32)
+    shot = iso_shot(nx, ny, nz, 4, 8, seed=2, src=src, receivers=rec, layered=False)
+    (u, _), tr = _run_gpu(fd, shot, 8)
+    ur, _, trr = oracle_problem(O, shot).iso_run(shot.v, 8)
+    assert max_rel(u, ur) <= 1e-4 and max_rel(tr, trr) <= 1e-4 and np.abs(ur).max() > 0
+
+
+def test_axis_beyond_the_launch_grid_is_refused(fd):
+    """2^20 points along y (the largest axis a description may have) need more
+    than 65535 tiles of 16 rows: creation reports it instead of launching."""
+    import torch
+    d, _ = fd.make_desc(fd.FD_MODE_ISO, 1, 1 << 20, 1, 4, 4, 10.0, 10.0, 1e-4)
+    nbytes = fd.fd_required_bytes(d)
+    arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda:0")
+    ptr = arena.data_ptr() + (-arena.data_ptr()) % 256
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_create_grid(d, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+    d2, _ = fd.make_desc(fd.FD_MODE_ISO, 1, 1, (1 << 20) + 1, 4, 4, 10.0, 10.0, 1e-4)
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_required_bytes(d2)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+
+
 def test_anisotropic_spacing(fd, O):
     shot = iso_shot(40, 36, 33, 4, 50, seed=11, nb=4, dz=7.0)
     (u, up), _ = _run_gpu(fd, shot, 50)
