@@ -91,6 +91,74 @@ def _oracle_slab_worker(rank, world, port, R, q):
         dist.destroy_process_group()
 
 
+def _vti_shot():
+    s = synth.vti_shot(24, nsteps=12, seed=5, with_model=False)
+    s.nz = 40
+    s.dzk, s.dz, s.nb = None, s.h, 0
+    s.src = (12, 11, 21)
+    s.receivers = synth.receiver_plane(24, 24, 9, stride=3)
+    s.v = synth.layered_model(24, 24, 40, 5)
+    s.eps, s.delta = synth.layered_anisotropy(40, 24, 24, 5)
+    return s
+
+
+def _oracle_vti_slab_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    import oracle.oracle as O
+    from paper_1410_1387_gb300 import dist as fdist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        shot = _vti_shot()
+        P = slabs.z_halo(shot)
+        sl = slabs.slab_bounds(shot.nz, world, P)[rank]
+        part, keep = slabs.slab_shot(shot, sl)
+        prob = oracle_problem(O, part)
+        z = np.zeros((part.nz, part.ny, part.nx))
+        p, pp, qq, qp = z.copy(), z.copy(), z.copy(), z.copy()
+        tr = np.zeros((shot.nsteps, len(keep)))
+        lower = rank - 1 if rank > 0 else None
+        upper = rank + 1 if rank < world - 1 else None
+        for n in range(shot.nsteps):
+            p, pp, qq, qp, t = prob.vti_run(part.v, part.eps, part.delta, 1, p, pp, qq, qp, n0=n)
+            if len(keep):
+                tr[n] = t[0]
+            fdist.halo_exchange(torch.from_numpy(p), P, lower, upper)
+            fdist.halo_exchange(torch.from_numpy(qq), P, lower, upper)
+        own = slice(sl.a - sl.lo, sl.b - sl.lo)
+        q.put((rank, p[own], qq[own], keep, tr))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_oracle_vti_slabs_over_gloo_match_the_unsplit_run(O):
+    """The paper's operator (R_xy = 12, R_z = 8, uniform dz) in two z slabs:
+    p and q exchanged, owned planes and traces equal to the unsplit run."""
+    import torch.multiprocessing as mp
+    shot = _vti_shot()
+    pr, _, qr, _, trr = oracle_problem(O, shot).vti_run(shot.v, shot.eps, shot.delta, shot.nsteps)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_oracle_vti_slab_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr_ in procs:
+        pr_.start()
+    out = sorted((q.get(timeout=300) for _ in procs), key=lambda x: x[0])
+    for pr_ in procs:
+        pr_.join(timeout=60)
+        assert pr_.exitcode == 0
+    assert np.array_equal(np.concatenate([o[1] for o in out]), pr)
+    assert np.array_equal(np.concatenate([o[2] for o in out]), qr)
+    tr = np.zeros_like(trr)
+    for o in out:
+        if len(o[3]):
+            tr[:, o[3]] = o[4]
+    assert np.array_equal(tr, trr) and np.abs(trr).max() > 0
+
+
 @pytest.mark.parametrize("R,world", [(4, 2), (4, 3), (8, 2)])
 def test_oracle_slabs_over_gloo_match_the_unsplit_run(O, R, world):
     import torch.multiprocessing as mp
