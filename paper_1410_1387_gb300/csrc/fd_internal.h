@@ -62,6 +62,7 @@ struct alignas(16) IsoArgs {
     DevState *st;
     unsigned int ncta;
     float c2dt;             // 2 dt: the gradient sweep's factor
+    int skip_plane1;        // test hook: 1 + a plane whose u^n copy CTA (0,0,0) withholds (0 = none)
 };
 
 // Arguments of the VTI sweep (Eqs. 1-2, 4-5).

@@ -137,7 +137,15 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             prefetch_tmap(tm_kappa);
             int a_end = z0, b_end = z0;             // planes issued: A [z0, a_end), B [z0, b_end)
             bool ok = true;
+            // test hook (fd_debug_skip_copy): CTA (0,0,0) withholds one plane's copy,
+            // so that its consumers' bounded wait runs out and the launch reports a
+            // timeout; every wait on that path is bounded
+            const int skip = (bx == 0 && by == 0 && bz == 0) ? a.skip_plane1 - 1 : -1;
             auto issue_a = [&](int p) {
+                if (p == skip) {
+                    a_end = p + 1;
+                    return;
+                }
                 const int u = p - z0, s = u % C::NA;
                 if (u >= C::NA && !mbar_wait_bounded(&emptyA[s], ((u / C::NA) - 1) & 1, kWaitLimit)) {
                     ok = false;

@@ -42,6 +42,7 @@ EXPORTS = [
     "fd_batch_steps_left", "fd_batch_run", "fd_batch_destroy",
     "fd_set_injection", "fd_adjoint_source", "fd_grad_accumulate",
     "fd_set_z_window", "fd_halo_exchange", "fd_optimized_weights", "fd_set_weights",
+    "fd_debug_skip_copy",
 ]
 
 
@@ -121,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "fd_halo_exchange": [_vp, _vp, _i],
             "fd_optimized_weights": [_i, _d, _vp],
             "fd_set_weights": [_vp, _vp, _vp],
+            "fd_debug_skip_copy": [_vp, _i],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -296,6 +298,10 @@ def fd_set_weights(g, w_xy=None, w_z=None) -> None:
     a = None if w_xy is None else np.ascontiguousarray(w_xy, dtype=np.float64)
     b = None if w_z is None else np.ascontiguousarray(w_z, dtype=np.float64)
     _check(lib().fd_set_weights(g, _ptr(a), _ptr(b)))
+
+
+def fd_debug_skip_copy(g, plane: int) -> None:
+    _check(lib().fd_debug_skip_copy(g, plane))
 
 
 def fd_set_z_window(g, kg0: int, nz_global: int) -> None:

@@ -272,6 +272,30 @@ def test_error_codes(fd):
     g.close()
 
 
+def test_bounded_wait_reports_timeout(fd, O):
+    """Failure detection without a GPU fault: one CTA is denied one plane's TMA
+    copy (the test hook), its bounded wait runs out after about a second, it
+    records the timeout and exits; fd_sync reports FD_ERR_TIMEOUT and the
+    context keeps working (a fresh grid's run still matches the oracle)."""
+    import time
+    shot = iso_shot(64, 32, 40, 4, 6, seed=3, nb=4)
+    g = fd.grid_from_shot(shot, device="cuda:0")
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_debug_skip_copy(g.h, 40)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+    fd.fd_debug_skip_copy(g.h, 6)         # CTA (0,0,0) covers planes 0..35 of u^n
+    t0 = time.perf_counter()
+    g.run(1)
+    with pytest.raises(fd.FdError) as e:
+        g.sync()
+    assert e.value.code == fd.FD_ERR_TIMEOUT and "timed out" in str(e.value)
+    assert 0.5 < time.perf_counter() - t0 < 30.0
+    g.close()
+    (u, _), tr = _run_gpu(fd, shot, shot.nsteps)
+    ur, _, _ = oracle_problem(O, shot).iso_run(shot.v, shot.nsteps)
+    assert max_rel(u, ur) <= 1e-4
+
+
 @pytest.mark.parametrize("R", [4, 8])
 def test_full_size_512_one_step_sampled(fd, O, R):
     """The 512^3 layered shot in the benchmark's launch configuration: after 30
