@@ -236,7 +236,7 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
         a.cur = g->field[cur];
         a.skip_plane1 = g->debug_skip + 1;
         g->debug_skip = -1;
-        const IsoMaps maps{g->tm_halo[cur], g->tm_tile[1 - cur], g->tm_model[0]};
+        const IsoMaps maps{g->tm_halo[cur], g->tm_tile[1 - cur], g->tm_model[0], g->tm_tile[cur]};
         e = launch_iso(d.r_xy, g->L, maps, a, s);
         newbuf = a.prev;
     } else {
@@ -762,7 +762,8 @@ int fd_grad_accumulate(fd_grid_t *g, const float *z, const float *a, float *grad
     const Launch L = iso_grad_launch(R, d.nx, d.ny, d.nz);
     IsoMaps maps;
     CUtensorMap mg;
-    if (cached_map(g, a, L.tx + 2 * R, L.ty + 2 * R, &maps.cur) || cached_map(g, z, L.tx, L.ty, &maps.prev) ||
+    if (cached_map(g, a, L.tx + 2 * R, L.ty + 2 * R, &maps.cur) || cached_map(g, a, L.tx, L.ty, &maps.cur_tile) ||
+        cached_map(g, z, L.tx, L.ty, &maps.prev) ||
         cached_map(g, g->model[0], L.tx, L.ty, &maps.kappa) || cached_map(g, grad, L.tx, L.ty, &mg))
         return fail(FD_ERR_CUDA, "tensor map encoding failed");
     IsoArgs w = iso_args(g);
@@ -1217,7 +1218,7 @@ int fd_batch_create(void *stream, fd_batch_t **out)
     if (!b) return fail(FD_ERR_NO_MEMORY, "host allocation failed");
     b->stream = static_cast<cudaStream_t>(stream);
     b->L[0] = Launch{64, 16, 64, 3};
-    b->L[1] = Launch{64, 8, 64, 2};
+    b->L[1] = Launch{32, 16, 64, 2};
     *out = b;
     return FD_OK;
 }

@@ -94,13 +94,14 @@ struct Launch {
 // Largest z chunk of one CTA (its damping factors are staged in shared memory).
 constexpr int kMaxChunk = 1024;
 
-// Planes per CTA: enough CTAs (about 2048) for several waves over 152 SMs, at
-// least 32 planes per chunk (measured: shorter chunks lose more to priming the
-// z queue and filling the pipeline than they gain in waves), at most kMaxChunk.
-inline int default_zchunk(const Launch &L, int nx, int ny, int nz)
+// Planes per CTA: enough CTAs (about `target`, 2048 by default) for several
+// waves over 152 SMs, at least 32 planes per chunk (measured: shorter chunks lose
+// more to priming the z queue and filling the pipeline than they gain in
+// waves), at most kMaxChunk.
+inline int default_zchunk(const Launch &L, int nx, int ny, int nz, long target = 2048)
 {
     const long tiles = (long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
-    long chunks = (2048 + tiles - 1) / tiles;
+    long chunks = (target + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
     int zc = (int)((nz + chunks - 1) / chunks);
     const int lo = nz < 32 ? nz : 32;
@@ -111,6 +112,7 @@ inline int default_zchunk(const Launch &L, int nx, int ny, int nz)
 // Tensor maps of one isotropic launch: u^n with the R halo, u^{n-1} and kappa tiles.
 struct IsoMaps {
     CUtensorMap cur, prev, kappa;
+    CUtensorMap cur_tile;   // u^n with the tile box (radius 8 streams its z-queue entries through it)
 };
 
 // 3D tensor map over a pitched nx x ny x nz float field, box (bx, by, 1).

@@ -148,6 +148,7 @@ extern "C" int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u
     int cr = encode_field_map(&tm.cur, u_cur, d->nx, d->ny, d->nz, lay.pitch, L.tx + 2 * R, L.ty + 2 * R);
     if (!cr) cr = encode_field_map(&tm.prev, u_prev, d->nx, d->ny, d->nz, lay.pitch, L.tx, L.ty);
     if (!cr) cr = encode_field_map(&tm.kappa, kappa, d->nx, d->ny, d->nz, lay.pitch, L.tx, L.ty);
+    if (!cr) cr = encode_field_map(&tm.cur_tile, u_cur, d->nx, d->ny, d->nz, lay.pitch, L.tx, L.ty);
     if (cr) return err(FD_ERR_CUDA, "tensor map encoding failed");
 
     IsoArgs a{};

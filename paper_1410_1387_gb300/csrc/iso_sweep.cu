@@ -42,8 +42,14 @@ struct IsoCfg {
     static constexpr int SW = TX + 2 * R;           // staged row width (floats)
     static constexpr int SH = TY + 2 * R;           // staged rows
     static constexpr int SLOT_A = SW * SH;          // floats per u^n plane
-    static constexpr int SLOT_B = NBT * TX * TY;    // floats per ring B plane
-    static constexpr int NA = R + 1 + LA;           // ring A slots
+    // QB (radius 8): each plane's own values for the z queue arrive as one more
+    // ring B tile (u^n of plane k + R), so ring A holds only the planes in
+    // flight rather than R planes ahead: the shared memory of three CTAs per SM
+    static constexpr bool QB = R >= 8;
+    static constexpr int NBT_ALL = NBT + (QB ? 1 : 0);
+    static constexpr int SLOT_B = NBT_ALL * TX * TY;   // floats per ring B plane
+    static constexpr int NA = QB ? LA + 1 : R + 1 + LA;   // ring A slots
+    static constexpr int MINB = QB ? 3 : 2;         // CTAs per SM the registers are budgeted for
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
@@ -88,9 +94,9 @@ __device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_
 // gets grad += a.c2dt z (L a) / sqrt(kappa), written over the gradient (`prev`).
 template <int R, int TX, int TY, int LA, bool INJ, bool GRAD = false>
 __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtensorMap *tm_prev,
-                                         const CUtensorMap *tm_kappa, const IsoArgs &a, float *prev,
-                                         const float *cur, const int n, const int bx, const int by, const int bz,
-                                         const CUtensorMap *tm_grad = nullptr)
+                                         const CUtensorMap *tm_kappa, const CUtensorMap *tm_ctile, const IsoArgs &a,
+                                         float *prev, const float *cur, const int n, const int bx, const int by,
+                                         const int bz, const CUtensorMap *tm_grad = nullptr)
 {
     using C = IsoCfg<R, TX, TY, LA, GRAD ? 3 : 2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -135,6 +141,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             prefetch_tmap(tm_cur);
             prefetch_tmap(tm_prev);
             prefetch_tmap(tm_kappa);
+            if (C::QB) prefetch_tmap(tm_ctile);
             int a_end = z0, b_end = z0;             // planes issued: A [z0, a_end), B [z0, b_end)
             bool ok = true;
             // test hook (fd_debug_skip_copy): CTA (0,0,0) withholds one plane's copy,
@@ -166,13 +173,23 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 tma_load_3d(dst, tm_prev, &fullB[s], x0, y0, k);
                 tma_load_3d(dst + TX * TY, tm_kappa, &fullB[s], x0, y0, k);
                 if (GRAD) tma_load_3d(dst + 2 * TX * TY, tm_grad, &fullB[s], x0, y0, k);
+                // the z-queue entry: plane k + R (zeros past the grid)
+                if (C::QB) tma_load_3d(dst + (C::NBT_ALL - 1) * TX * TY, tm_ctile, &fullB[s], x0, y0, k + R);
                 b_end = k + 1;
             };
-            for (int p = z0; ok && p < min(z0 + R, zend); ++p) issue_a(p);
-            for (int t = z0; ok && t < z1; ++t) {
-                if (*sh_abort) break;
-                if (t + R < zend) issue_a(t + R);
-                if (ok) issue_b(t);
+            if (C::QB) {
+                for (int t = z0; ok && t < z1; ++t) {
+                    if (*sh_abort) break;
+                    issue_a(t);
+                    if (ok) issue_b(t);
+                }
+            } else {
+                for (int p = z0; ok && p < min(z0 + R, zend); ++p) issue_a(p);
+                for (int t = z0; ok && t < z1; ++t) {
+                    if (*sh_abort) break;
+                    if (t + R < zend) issue_a(t + R);
+                    if (ok) issue_b(t);
+                }
             }
             if (!ok) {
                 *sh_abort = 1;
@@ -204,7 +221,9 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         for (int m = 0; m < R; ++m) {
             const int p = z0 + m;
             float4 v = zero4;
-            if (ok && p < zend) {
+            if (C::QB) {
+                v = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
+            } else if (ok && p < zend) {
                 const int u = p - z0;
                 if (mbar_wait_bounded(&fullA[u % C::NA], (u / C::NA) & 1, kWaitLimit))
                     v = *reinterpret_cast<const float4 *>(ringA + (u % C::NA) * C::SLOT_A + own);
@@ -225,8 +244,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 ok = false;
                 break;
             }
-            // my values of plane k + R enter the queue
-            {
+            // my values of plane k + R enter the queue (QB: from ring B, below)
+            if (!C::QB) {
                 const int p = k + R;
                 float4 v = zero4;
                 if (p < zend) {
@@ -245,6 +264,15 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 break;
             }
             const float *tb = ringB + sb * C::SLOT_B;
+            if (C::QB) {
+                q[2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
+                // plane k of u^n in ring A (without QB its wait happened when it
+                // entered the z queue, R planes ago)
+                if (!mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit)) {
+                    ok = false;
+                    break;
+                }
+            }
             const float4 pv = *reinterpret_cast<const float4 *>(tb + ownb);
             const float4 kv = *reinterpret_cast<const float4 *>(tb + TX * TY + ownb);
             const float4 gv = GRAD ? *reinterpret_cast<const float4 *>(tb + 2 * TX * TY + ownb) : zero4;
@@ -395,14 +423,15 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 
 
 template <int R, int TX, int TY, int LA, bool INJ>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::MINB))
     iso_sweep_kernel(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
-                     const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ IsoArgs a)
+                     const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_ctile,
+                     const __grid_constant__ IsoArgs a)
 {
     using C = IsoCfg<R, TX, TY, LA>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int n = step_prologue(a.st, a.ncta, 0x7fffffff, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
-    iso_body<R, TX, TY, LA, INJ>(&tm_cur, &tm_prev, &tm_kappa, a, a.prev, a.cur, n, blockIdx.x, blockIdx.y,
+    iso_body<R, TX, TY, LA, INJ>(&tm_cur, &tm_prev, &tm_kappa, &tm_ctile, a, a.prev, a.cur, n, blockIdx.x, blockIdx.y,
                                  blockIdx.z);
 }
 
@@ -412,7 +441,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
 // of these launches replays without per-step arguments.  Shots that reached
 // their last step skip their items.
 template <int R, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::MINB))
     iso_batch_kernel(const int4 *__restrict__ items, const BatchShot *__restrict__ shots)
 {
     using C = IsoCfg<R, TX, TY, LA>;
@@ -428,7 +457,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     const int n = step_prologue(b.a.st, b.ncta, b.n_end, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
     if (n < 0) return;
     const int c = b.cur0 ^ ((n - b.n0) & 1);      // buffer holding u^n
-    iso_body<R, TX, TY, LA, false>(&b.halo[c], &b.tile[c ^ 1], &b.kappa, *sa, b.buf[c ^ 1], b.buf[c], n, it.y,
+    iso_body<R, TX, TY, LA, false>(&b.halo[c], &b.tile[c ^ 1], &b.kappa, &b.tile[c], *sa, b.buf[c ^ 1], b.buf[c], n, it.y,
                                    it.z, it.w);
 }
 
@@ -452,7 +481,7 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
     const int smem = C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4);
-    iso_sweep_kernel<R, TX, TY, LA, INJ><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, a);
+    iso_sweep_kernel<R, TX, TY, LA, INJ><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, tm.cur_tile, a);
     return cudaGetLastError();
 }
 
@@ -486,13 +515,13 @@ static cudaError_t launch_b(const int4 *items, int nitems, const BatchShot *shot
 // pipeline over a = u^n, with z, kappa and the gradient in ring B.  It does not
 // advance the grid's time index.
 template <int R, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA, 3>::MINB))
     iso_grad_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_z,
                     const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_grad,
-                    const __grid_constant__ IsoArgs a)
+                    const __grid_constant__ CUtensorMap tm_atile, const __grid_constant__ IsoArgs a)
 {
-    iso_body<R, TX, TY, LA, false, true>(&tm_a, &tm_z, &tm_kappa, a, a.prev, a.cur, 0, blockIdx.x, blockIdx.y,
-                                         blockIdx.z, &tm_grad);
+    iso_body<R, TX, TY, LA, false, true>(&tm_a, &tm_z, &tm_kappa, &tm_atile, a, a.prev, a.cur, 0, blockIdx.x,
+                                         blockIdx.y, blockIdx.z, &tm_grad);
 }
 
 template <int R, int TX, int TY, int LA>
@@ -513,22 +542,20 @@ static cudaError_t launch_g(const IsoMaps &tm, const CUtensorMap &tm_grad, const
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
     const int smem = C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4);
-    iso_grad_kernel<R, TX, TY, LA><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, tm_grad, a);
+    iso_grad_kernel<R, TX, TY, LA><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, tm_grad, tm.cur_tile, a);
     return cudaGetLastError();
 }
 
 Launch iso_grad_launch(int R, int nx, int ny, int nz)
 {
-    Launch L = R == 4 ? Launch{64, 16, 0, 3} : Launch{64, 8, 0, 2};
-    L.zchunk = default_zchunk(L, nx, ny, nz);
-    return L;
+    return iso_default_launch(R, nx, ny, nz);
 }
 
 cudaError_t launch_iso_grad(int R, const Launch &L, const IsoMaps &tm, const CUtensorMap &tm_grad, const IsoArgs &a,
                             cudaStream_t s)
 {
     if (R == 4 && L.tx == 64 && L.ty == 16 && L.lookahead == 3) return launch_g<4, 64, 16, 3>(tm, tm_grad, a, s);
-    if (R == 8 && L.tx == 64 && L.ty == 8 && L.lookahead == 2) return launch_g<8, 64, 8, 2>(tm, tm_grad, a, s);
+    if (R == 8 && L.tx == 32 && L.ty == 16 && L.lookahead == 2) return launch_g<8, 32, 16, 2>(tm, tm_grad, a, s);
     return cudaErrorInvalidConfiguration;
 }
 
@@ -580,12 +607,14 @@ Launch iso_default_launch(int R, int nx, int ny, int nz)
         L.tx = 64;
         L.ty = 16;
         L.lookahead = 3;
+        L.zchunk = default_zchunk(L, nx, ny, nz);
     } else {
-        L.tx = 64;
-        L.ty = 8;
+        // three CTAs per SM: about 4096 CTAs make several waves with a short tail
+        L.tx = 32;
+        L.ty = 16;
         L.lookahead = 2;
+        L.zchunk = default_zchunk(L, nx, ny, nz, 4096);
     }
-    L.zchunk = default_zchunk(L, nx, ny, nz);
     return L;
 }
 
