@@ -6,15 +6,16 @@
 // queue of Sec. 3, rebuilt for sm_103a as a warp-specialised TMA pipeline):
 //   * a CTA owns a TX x TY column of the grid and a chunk of z planes;
 //   * one producer warp issues TMA 3D tile loads into two shared-memory rings:
-//     ring A holds plane p of u^n with an R-cell x-y halo (loads outside the
+//     ring A holds plane k of u^n with an R-cell x-y halo (loads outside the
 //     grid return zeros: the zero halo of Sec. 1 at no cost), ring B holds the
-//     TX x TY tiles of u^{n-1} and kappa of plane k.  Each slot has a "full"
-//     mbarrier (TMA transaction count) and an "empty" mbarrier (one arrival per
-//     consumer warp), so consumer warps never wait for each other and the
-//     producer runs up to LA planes ahead;
+//     TX x TY tiles of u^{n-1} and kappa of plane k and of u^n of plane k + R.
+//     Each slot has a "full" mbarrier (TMA transaction count) and an "empty"
+//     mbarrier (one arrival per consumer warp), so consumer warps never wait
+//     for each other and the producer runs up to LA planes ahead;
 //   * each consumer thread owns 4 consecutive x points (one float4) of one row
-//     and keeps their 2R+1 z neighbours in registers; x and y neighbours come
-//     from the staged plane (x as 1 + R/2 aligned float4 reads, y as 2R);
+//     and keeps their 2R+1 z neighbours in registers (plane k + R enters from
+//     ring B); x and y neighbours come from the staged plane (x as 1 + R/2
+//     aligned float4 reads, y as 2R);
 //   * u^{n+1} is written in place over u^{n-1} with 128-bit evict-first stores
 //     (each point's older value was staged before any thread writes it);
 //   * the damping is applied in its deferred form G (2u - G u_prev + kappa Lu + s),
@@ -42,14 +43,15 @@ struct IsoCfg {
     static constexpr int SW = TX + 2 * R;           // staged row width (floats)
     static constexpr int SH = TY + 2 * R;           // staged rows
     static constexpr int SLOT_A = SW * SH;          // floats per u^n plane
-    // QB (radius 8): each plane's own values for the z queue arrive as one more
-    // ring B tile (u^n of plane k + R), so ring A holds only the planes in
-    // flight rather than R planes ahead: the shared memory of three CTAs per SM
-    static constexpr bool QB = R >= 8;
-    static constexpr int NBT_ALL = NBT + (QB ? 1 : 0);
+    // Each plane's own values for the z queue arrive as one more ring B tile
+    // (u^n of plane k + R), so ring A holds only the LA + 1 planes in flight
+    // rather than R planes ahead: small enough for three (radius 8) or four
+    // (radius 4) CTAs of 160 threads per SM.
+    static constexpr int NBT_ALL = NBT + 1;
     static constexpr int SLOT_B = NBT_ALL * TX * TY;   // floats per ring B plane
-    static constexpr int NA = QB ? LA + 1 : R + 1 + LA;   // ring A slots
-    static constexpr int MINB = QB ? 3 : 2;         // CTAs per SM the registers are budgeted for
+    static constexpr int NA = LA + 1;               // ring A slots
+    // CTAs per SM the registers are budgeted for
+    static constexpr int MINB = (TX / 4) * TY + 32 <= 160 ? (R >= 8 ? 3 : 4) : 2;
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
@@ -113,7 +115,6 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
     const int x0 = bx * TX, y0 = by * TY;
     const int z0 = bz * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.nz);
-    const int zend = min(z1 + R, a.nz);             // ring A planes: [z0, zend)
 
     if (tid == 0) {
         for (int s = 0; s < C::NA; ++s) {
@@ -141,7 +142,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             prefetch_tmap(tm_cur);
             prefetch_tmap(tm_prev);
             prefetch_tmap(tm_kappa);
-            if (C::QB) prefetch_tmap(tm_ctile);
+            prefetch_tmap(tm_ctile);
             int a_end = z0, b_end = z0;             // planes issued: A [z0, a_end), B [z0, b_end)
             bool ok = true;
             // test hook (fd_debug_skip_copy): CTA (0,0,0) withholds one plane's copy,
@@ -174,22 +175,13 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 tma_load_3d(dst + TX * TY, tm_kappa, &fullB[s], x0, y0, k);
                 if (GRAD) tma_load_3d(dst + 2 * TX * TY, tm_grad, &fullB[s], x0, y0, k);
                 // the z-queue entry: plane k + R (zeros past the grid)
-                if (C::QB) tma_load_3d(dst + (C::NBT_ALL - 1) * TX * TY, tm_ctile, &fullB[s], x0, y0, k + R);
+                tma_load_3d(dst + (C::NBT_ALL - 1) * TX * TY, tm_ctile, &fullB[s], x0, y0, k + R);
                 b_end = k + 1;
             };
-            if (C::QB) {
-                for (int t = z0; ok && t < z1; ++t) {
-                    if (*sh_abort) break;
-                    issue_a(t);
-                    if (ok) issue_b(t);
-                }
-            } else {
-                for (int p = z0; ok && p < min(z0 + R, zend); ++p) issue_a(p);
-                for (int t = z0; ok && t < z1; ++t) {
-                    if (*sh_abort) break;
-                    if (t + R < zend) issue_a(t + R);
-                    if (ok) issue_b(t);
-                }
+            for (int t = z0; ok && t < z1; ++t) {
+                if (*sh_abort) break;
+                issue_a(t);
+                if (ok) issue_b(t);
             }
             if (!ok) {
                 *sh_abort = 1;
@@ -220,17 +212,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             const int p = z0 + m;
-            float4 v = zero4;
-            if (C::QB) {
-                v = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
-            } else if (ok && p < zend) {
-                const int u = p - z0;
-                if (mbar_wait_bounded(&fullA[u % C::NA], (u / C::NA) & 1, kWaitLimit))
-                    v = *reinterpret_cast<const float4 *>(ringA + (u % C::NA) * C::SLOT_A + own);
-                else
-                    ok = false;
-            }
-            q[R + m] = v;
+            q[R + m] = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
         }
         float4 g4 = zero4;
         float gyv = 0.f;
@@ -244,34 +226,18 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 ok = false;
                 break;
             }
-            // my values of plane k + R enter the queue (QB: from ring B, below)
-            if (!C::QB) {
-                const int p = k + R;
-                float4 v = zero4;
-                if (p < zend) {
-                    const int u = p - z0;
-                    if (!mbar_wait_bounded(&fullA[u % C::NA], (u / C::NA) & 1, kWaitLimit)) {
-                        ok = false;
-                        break;
-                    }
-                    v = *reinterpret_cast<const float4 *>(ringA + (u % C::NA) * C::SLOT_A + own);
-                }
-                q[2 * R] = v;
-            }
             const int ub = k - z0, sb = ub % C::NB;
             if (!mbar_wait_bounded(&fullB[sb], (ub / C::NB) & 1, kWaitLimit)) {
                 ok = false;
                 break;
             }
             const float *tb = ringB + sb * C::SLOT_B;
-            if (C::QB) {
-                q[2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
-                // plane k of u^n in ring A (without QB its wait happened when it
-                // entered the z queue, R planes ago)
-                if (!mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit)) {
-                    ok = false;
-                    break;
-                }
+            // my values of plane k + R enter the queue
+            q[2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
+            // plane k of u^n with its halo, in ring A
+            if (!mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit)) {
+                ok = false;
+                break;
             }
             const float4 pv = *reinterpret_cast<const float4 *>(tb + ownb);
             const float4 kv = *reinterpret_cast<const float4 *>(tb + TX * TY + ownb);
