@@ -56,10 +56,12 @@ _I = ctypes.POINTER(ctypes.c_int)
 
 
 def lib():
+    """The oracle's library; FD_ORACLE_LIB names another build of oracle.c to load
+    instead (the mutation test loads copies with planted mistakes this way)."""
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            L = ctypes.CDLL(os.environ.get("FD_ORACLE_LIB") or build())
             L.or_taylor_weights.argtypes = [ctypes.c_int, _D]
             L.or_lagrange_d2.argtypes = [_D, ctypes.c_int, ctypes.c_int, _D]
             L.or_z_table.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_double, _D]

@@ -46,6 +46,33 @@ def test_iso_plane_wave_dispersion(O):
     np.testing.assert_allclose(up[s, s, s], np.cos(phase - (steps - 1) * w * dt)[s, s, s], atol=2e-12)
 
 
+def test_iso_plane_wave_dispersion_custom_weights(O):
+    """The same closed form with caller-supplied weights (band-optimised, and
+    different on x-y and z): the symbol is the one of those weights."""
+    R, n, steps = 4, 40, 3
+    h, v = 10.0, 2000.0
+    dt = 0.35 * O.iso_courant_limit(R) * h / v
+    wxy, wz = O.optimized_weights(R, 2.0), O.optimized_weights(R, 1.2)
+    K = lambda c, t: -(c[0] + 2 * sum(c[l] * math.cos(l * t) for l in range(1, R + 1)))  # noqa: E731
+    th = np.array([0.7, 0.4, 1.1])             # k_a h
+    lam = (v * dt / h) ** 2 * (K(wxy, th[0]) + K(wxy, th[1]) + K(wz, th[2]))
+    w = 2.0 * math.asin(math.sqrt(lam) / 2.0) / dt
+    i = np.arange(n)
+    phase = (th[2] * i[:, None, None] + th[1] * i[None, :, None] + th[0] * i[None, None, :])
+    P = O.Problem(n, n, n, r_xy=R, h=h, dt=dt, weights_xy=wxy, weights_z=wz)
+    u, up, _ = P.iso_run(np.full((n, n, n), v), steps, u=np.cos(phase), uprev=np.cos(phase + w * dt),
+                         traces=False)
+    s = slice(R * steps, n - R * steps)
+    np.testing.assert_allclose(u[s, s, s], np.cos(phase - steps * w * dt)[s, s, s], atol=2e-12)
+    # Taylor weights passed explicitly give the default run exactly
+    u0 = np.cos(phase)
+    a = O.Problem(n, n, n, r_xy=R, h=h, dt=dt).iso_run(np.full((n, n, n), v), 2, u=u0, traces=False)[0]
+    tw = O.taylor_weights(R)
+    b = O.Problem(n, n, n, r_xy=R, h=h, dt=dt, weights_xy=tw, weights_z=tw).iso_run(
+        np.full((n, n, n), v), 2, u=u0, traces=False)[0]
+    assert np.array_equal(a, b)
+
+
 def test_vti_plane_wave_dispersion(O):
     rxy, rz, n, steps = 4, 2, 36, 2
     h, dz = 10.0, 8.0
