@@ -99,6 +99,35 @@ def test_extreme_aspect_ratios(fd, O, shape):
     assert max_rel(u, ur) <= 1e-4 and max_rel(tr, trr) <= 1e-4 and np.abs(ur).max() > 0
 
 
+def test_grid_beyond_2_to_the_31_points(fd):
+    """1024 x 1024 x 2100 points (2.2e9 > 2^31, 26 GiB of arena): after 20 steps
+    the values around the source equal, bit for bit, those of a 200^3 grid with
+    the same source (the wave has not reached any boundary of either), so every
+    offset of the big grid is formed in 64 bits."""
+    import torch
+    R, steps, c = 4, 20, 40
+    h, v, dt = 10.0, 2000.0, 0.5 * synth.COURANT_LIMIT[4] * 10.0 / 2000.0
+
+    def run(nx, ny, nz, src):
+        spec = fd.GridSpec(fd.FD_MODE_ISO, nx, ny, nz, R, R, h, h, dt)
+        g = fd.Grid(spec, device="cuda:0")
+        g.set_model(torch.full((nz, ny, nx), v, dtype=torch.float32, device="cuda:0"))
+        g.add_source(*src)
+        g.run(steps)
+        g.sync()
+        sx, sy, sz = src
+        u = g.field_view(0)[sz - c:sz + c, sy - c:sy + c, sx - c:sx + c].cpu().numpy()
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+        return u
+
+    big = run(1024, 1024, 2100, (512, 512, 1050))
+    small = run(200, 200, 200, (100, 100, 100))
+    assert np.abs(small).max() > 0
+    np.testing.assert_array_equal(big, small)
+
+
 def test_axis_beyond_the_launch_grid_is_refused(fd):
     """2^20 points along y (the largest axis a description may have) need more
     than 65535 tiles of 16 rows: creation reports it instead of launching."""
