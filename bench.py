@@ -9,7 +9,9 @@ operator (R_xy = 12, R_z = 8) are selectable with --workload.
 
 Prints one JSON line.  `value` is grid-point updates per second with all
 inputs resident in HBM (three 512 MiB fields per shot: larger than L2, so no
-flush is needed between steps), timed with CUDA events on the grid's stream.
+flush is needed between steps), timed with CUDA events on the grid's stream
+over exactly --steps steps, after --settle seconds of untimed steps (steady
+state) and --warmup warm-up steps.
 `e2e` is one whole shot through the C ABI from pinned host memory: model
 upload, steps, receiver traces back to the host.  `roofline` compares the
 stencil kernel's algorithmic bytes per launch with the measured HBM copy
@@ -62,6 +64,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default="", help="tx,ty,zchunk,lookahead override")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--settle", type=float, default=1.5,
+                    help="seconds of untimed steps before the warm-up (steady state)")
     return ap.parse_args()
 
 
@@ -255,6 +259,22 @@ def measured_peak():
 
 # ---------------------------------------------------------------------------
 
+def device_info(dev) -> dict:
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    info = {"name": p.name, "sms": p.multi_processor_count, "memory_gib": round(p.total_memory / 2**30, 1)}
+    for k in ("L2_cache_size", "uuid"):
+        if hasattr(p, k):
+            info[k.lower()] = str(getattr(p, k))
+    try:
+        bus = subprocess.run(["nvidia-smi", f"--id={dev.index or 0}", "--query-gpu=pci.bus_id,ecc.errors.corrected.volatile.total",
+                              "--format=csv,noheader"], capture_output=True, text=True, timeout=20).stdout.strip()
+        info["pci_bus_and_ecc"] = bus
+    except Exception:
+        pass
+    return info
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -301,18 +321,29 @@ def run_ours(args):
     pts = shot.nx * shot.ny * shot.nz
 
     # ---- device-resident timing -------------------------------------------------
-    g = fd.grid_from_shot(shot, device=dev, nt_cap=K + W)
+    g = fd.grid_from_shot(shot, device=dev, receivers=False)
     if args.launch:
         g.set_launch(*[int(x) for x in args.launch.split(",")])
     stream = g.stream
-    g.run(W)
-    g.sync()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+    settle = 0
     with ClockSampler(local) as clk:
+        # Settle: untimed steps for at least args.settle seconds of sustained load
+        # before the warm-up, so that the timed steps run in the GPU's steady
+        # state (some boxes slow down for about a second shortly after a heavy
+        # load starts, then recover).  The receivers join afterwards.
+        t_set = time.perf_counter()
+        while time.perf_counter() - t_set < args.settle:
+            g.run(32)
+            g.sync()
+            settle += 32
+        g.set_receivers(shot.receivers, K + W)
+        g.run(W)
+        g.sync()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
         ev0.record(stream)
         g.run(K)
         ev1.record(stream)
@@ -381,9 +412,12 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": el_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": workload_config(args.workload, shot, args),
+        "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(args.workload, shot, args),
+                       settle={"seconds": args.settle, "steps": settle,
+                               "note": "untimed steps before the warm-up, for the steady state"}),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
-        "clocks": clk.summary(), "impl": "ours",
+        "clocks": clk.summary(), "device": device_info(dev), "impl": "ours",
     }
     print(json.dumps(line), flush=True)
     if world > 1:
