@@ -89,6 +89,8 @@ __device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_
 }
 
 // One CTA's work: tile (bx, by), z chunk bz, of the step u^n -> u^{n+1}.
+// tm_cur maps u^n with the halo box (ring A), tm_ctile u^n with the tile box
+// (the z-queue entries in ring B), tm_prev and tm_kappa the other ring B tiles.
 // INJ compiles in the injection lattice (adjoint runs only: the extra branch
 // in the store path costs about 6 % when present).  GRAD turns the sweep into
 // the adjoint's velocity-gradient term: `cur` is the forward level a = u^n,
