@@ -52,10 +52,15 @@ struct IsoCfg {
     static constexpr int NA = LA + 1;               // ring A slots
     // CTAs per SM the registers are budgeted for
     static constexpr int MINB = (TX / 4) * TY + 32 <= 160 ? (R >= 8 ? 3 : 4) : 2;
+    // Radius 8 in 32 x 16 tiles keeps its z queue in tensor memory instead of
+    // registers (the forward sweep; the adjoint's injection and gradient forms
+    // keep the register queue): 64 registers freed, four CTAs per SM.
+    static constexpr bool TQ_TILE = (R == 8 && TX == 32 && TY == 16);
+    static constexpr int minb(bool tq) { return tq ? 4 : MINB; }
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
-    static constexpr int OFF_GZ = OFF_BAR + 8 * (2 * NA + 2 * NB) + 16;
+    static constexpr int OFF_GZ = OFF_BAR + 8 * (2 * NA + 2 * NB) + 32;
     // + 4 bytes per plane of the chunk (damping factors along z), added at launch
     static constexpr int SMEM = OFF_GZ;
     static_assert(TX % 4 == 0 && R % 4 == 0, "x alignment");
@@ -103,6 +108,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                                          const int bz, const CUtensorMap *tm_grad = nullptr)
 {
     using C = IsoCfg<R, TX, TY, LA, GRAD ? 3 : 2>;
+    constexpr bool TQ = C::TQ_TILE && !INJ && !GRAD;
+    static_assert(!TQ || (R == 8 && C::NCW == 4), "tensor-memory queue: 16-plane ring, one warp per lane quarter");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ringA = reinterpret_cast<float *>(smem_raw);
     float *ringB = reinterpret_cast<float *>(smem_raw + C::OFF_B);
@@ -110,7 +117,9 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
     uint64_t *emptyA = fullA + C::NA;
     uint64_t *fullB = emptyA + C::NA;
     uint64_t *emptyB = fullB + C::NB;
-    int *sh = reinterpret_cast<int *>(emptyB + C::NB);   // [0] n, [1] abort, [2..3] issue counts
+    // [0] n, [1] abort, [2..3] issue counts, [4] step_prologue's, [5] tensor-memory address
+    int *sh = reinterpret_cast<int *>(emptyB + C::NB);
+    uint32_t *sh_tmem = reinterpret_cast<uint32_t *>(sh + 5);
     volatile int *sh_abort = sh + 1;
 
     const int tid = threadIdx.x;
@@ -135,7 +144,13 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
     }
     float *sgz = reinterpret_cast<float *>(smem_raw + C::OFF_GZ);   // z damping factors of the chunk
     for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
+    if constexpr (TQ) {
+        __syncwarp();
+        if (tid < 32) tmem_alloc(sh_tmem, 128);
+        tmem_fence_before_sync();
+    }
     __syncthreads();
+    if constexpr (TQ) tmem_fence_after_sync();
     bool failed = false;
 
     if (tid >= C::NC) {
@@ -203,18 +218,35 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         const int own = (ty + R) * C::SW + R + 4 * tx;   // my float4 in a ring A slot
         const int ownb = ty * TX + 4 * tx;               // my float4 in a ring B tile
 
-        // z queue: q[R + m] = my 4 values of plane k + m, m = -R..R
-        float4 q[2 * R + 1];
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const int p = z0 - R + m;
-            q[m] = (act && p >= 0) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
-        }
+        // z queue: q[R + m] = my 4 values of plane k + m, m = -R..R.
+        // Tensor-memory form: only q[0] (plane k + R, entering) is a register; my
+        // values of planes k - R .. k + R - 1 sit in my TMEM lane as a ring of 16
+        // slots of 4 columns, plane p in slot p mod 16, stored twice (columns
+        // 4 s and 64 + 4 s) so that the window of any plane is one contiguous run
+        // of 64 columns starting at its plane k - R.
+        float4 q[TQ ? 1 : 2 * R + 1];
+        uint32_t tq_lane = 0;
         bool ok = true;
+        if constexpr (TQ) {
+            tq_lane = *sh_tmem + ((uint32_t)(32 * (tid / 32)) << 16);
+            for (int m = 0; m < 2 * R; ++m) {
+                const int p = z0 - R + m;
+                const float4 v = (act && p >= 0 && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
+                const uint32_t c = tq_lane + 4 * (uint32_t)(p & 15);
+                __syncwarp();
+                tmem_st4x2(c, c + 64, v);
+            }
+        } else {
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const int p = z0 + m;
-            q[R + m] = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
+            for (int m = 0; m < R; ++m) {
+                const int p = z0 - R + m;
+                q[m] = (act && p >= 0) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
+            }
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                const int p = z0 + m;
+                q[R + m] = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
+            }
         }
         float4 g4 = zero4;
         float gyv = 0.f;
@@ -223,21 +255,25 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             gyv = a.gy[gyi];
         }
 
+        // With the tensor-memory queue every warp takes each branch as a whole
+        // (tcgen05 loads and stores are warp-collective), so the abort flag and the
+        // outcome of each bounded wait are agreed across the warp.
+        auto warp_all = [](bool v) { return TQ ? (bool)__all_sync(0xffffffffu, v) : v; };
         for (int k = z0; ok && k < z1; ++k) {
-            if (*sh_abort) {
+            if (!warp_all(*sh_abort == 0)) {
                 ok = false;
                 break;
             }
             const int ub = k - z0, sb = ub % C::NB;
-            if (!mbar_wait_bounded(&fullB[sb], (ub / C::NB) & 1, kWaitLimit)) {
+            if (!warp_all(mbar_wait_bounded(&fullB[sb], (ub / C::NB) & 1, kWaitLimit))) {
                 ok = false;
                 break;
             }
             const float *tb = ringB + sb * C::SLOT_B;
             // my values of plane k + R enter the queue
-            q[2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
+            q[TQ ? 0 : 2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
             // plane k of u^n with its halo, in ring A
-            if (!mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit)) {
+            if (!warp_all(mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit))) {
                 ok = false;
                 break;
             }
@@ -281,12 +317,26 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 mbar_arrive(&emptyA[sa]);
                 mbar_arrive(&emptyB[sb]);
             }
+            auto zpair = [&](int l, const float4 &up, const float4 &dn) {
+                lo = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo);
+                hi = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi);
+            };
+            if constexpr (TQ) {
+                // window of plane k: planes k - 8 + j at columns w0 + 4 j, j = 0..15
+                const uint32_t w0 = tq_lane + 4 * (uint32_t)((k - R) & 15);
+                float4 va[4], vb[4];
+                __syncwarp();
+                tmem_ld16x2(w0 + 16, w0 + 36, va, vb);     // planes k-4..k-1 and k+1..k+4
 #pragma unroll
-            for (int l = 1; l <= R; ++l) {
-                lo = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(q[R + l].x, q[R + l].y),
-                                                     make_float2(q[R - l].x, q[R - l].y)), lo);
-                hi = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(q[R + l].z, q[R + l].w),
-                                                     make_float2(q[R - l].z, q[R - l].w)), hi);
+                for (int l = 1; l <= 4; ++l) zpair(l, vb[l - 1], va[4 - l]);
+                tmem_ld16x2(w0, w0 + 48, va, vb);          // planes k-8..k-5 and k+4..k+7
+#pragma unroll
+                for (int l = 5; l <= 8; ++l) zpair(l, l == 8 ? q[0] : vb[l - 4], va[8 - l]);
+                // plane k + 8 takes the slot of plane k - 8, no longer needed
+                tmem_st4x2(w0, w0 + 64, q[0]);
+            } else {
+#pragma unroll
+                for (int l = 1; l <= R; ++l) zpair(l, q[R + l], q[R - l]);
             }
             acc[0] = lo.x;
             acc[1] = lo.y;
@@ -363,8 +413,10 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                     }
                 }
             }
+            if constexpr (!TQ) {
 #pragma unroll
-            for (int m = 0; m < 2 * R; ++m) q[m] = q[m + 1];
+                for (int m = 0; m < 2 * R; ++m) q[m] = q[m + 1];
+            }
         }
         if (!ok) {
             *sh_abort = 1;
@@ -372,7 +424,13 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         }
     }
 
-    if (__syncthreads_or(failed) && tid == C::NC) {
+    if constexpr (TQ) tmem_fence_before_sync();
+    const bool any_failed = __syncthreads_or(failed);
+    if constexpr (TQ) {
+        tmem_fence_after_sync();
+        if (tid < 32) tmem_dealloc(*sh_tmem, 128);
+    }
+    if (any_failed && tid == C::NC) {
         // A bounded wait gave up somewhere: record it, then wait (bounded) for the
         // copies still in flight so that none lands in shared memory after exit.
         atomicOr(&a.st->err, kErrTmaTimeout);
@@ -391,7 +449,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 
 
 template <int R, int TX, int TY, int LA, bool INJ>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::MINB))
+__global__ void __launch_bounds__((TX / 4) * TY + 32,
+                                  (IsoCfg<R, TX, TY, LA>::minb(IsoCfg<R, TX, TY, LA>::TQ_TILE && !INJ)))
     iso_sweep_kernel(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
                      const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_ctile,
                      const __grid_constant__ IsoArgs a)
@@ -409,7 +468,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::MI
 // of these launches replays without per-step arguments.  Shots that reached
 // their last step skip their items.
 template <int R, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::MINB))
+__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::minb(IsoCfg<R, TX, TY, LA>::TQ_TILE)))
     iso_batch_kernel(const int4 *__restrict__ items, const BatchShot *__restrict__ shots)
 {
     using C = IsoCfg<R, TX, TY, LA>;

@@ -301,18 +301,21 @@ def test_error_codes(fd):
     g.close()
 
 
-def test_bounded_wait_reports_timeout(fd, O):
+@pytest.mark.parametrize("R", [4, 8])
+def test_bounded_wait_reports_timeout(fd, O, R):
     """Failure detection without a GPU fault: one CTA is denied one plane's TMA
     copy (the test hook), its bounded wait runs out after about a second, it
     records the timeout and exits; fd_sync reports FD_ERR_TIMEOUT and the
-    context keeps working (a fresh grid's run still matches the oracle)."""
+    context keeps working (a fresh grid's run still matches the oracle).  At
+    radius 8 the CTA also frees its tensor memory on the way out: a CTA that
+    did not would leave the next launches unable to allocate."""
     import time
-    shot = iso_shot(64, 32, 40, 4, 6, seed=3, nb=4)
+    shot = iso_shot(64, 32, 40, R, 6, seed=3, nb=4)
     g = fd.grid_from_shot(shot, device="cuda:0")
     with pytest.raises(fd.FdError) as e:
         fd.fd_debug_skip_copy(g.h, 40)
     assert e.value.code == fd.FD_ERR_INVALID_ARG
-    fd.fd_debug_skip_copy(g.h, 6)         # CTA (0,0,0) covers planes 0..35 of u^n
+    fd.fd_debug_skip_copy(g.h, 6)         # CTA (0,0,0)'s z chunk is planes 0..31
     t0 = time.perf_counter()
     g.run(1)
     with pytest.raises(fd.FdError) as e:
