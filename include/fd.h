@@ -333,7 +333,7 @@ int fd_batch_create(void *stream, fd_batch_t **out);
 
 /* Tile (tx x ty, lookahead) and z chunk used for members of the given radius;
    zchunk 0 = each member grid's own (fd_set_launch).  Defaults: radius 4:
-   64 x 16, 64 planes, lookahead 3; radius 8: 32 x 16, 64 planes, lookahead 2. */
+   64 x 16, 64 planes, lookahead 3; radius 8: 32 x 32, 64 planes, lookahead 2. */
 int fd_batch_set_launch(fd_batch_t *b, int radius, int tx, int ty, int zchunk, int lookahead);
 
 /* Replay CUDA graphs of `steps` batch launches in fd_batch_run (0 = plain launches). */

@@ -1218,7 +1218,7 @@ int fd_batch_create(void *stream, fd_batch_t **out)
     if (!b) return fail(FD_ERR_NO_MEMORY, "host allocation failed");
     b->stream = static_cast<cudaStream_t>(stream);
     b->L[0] = Launch{64, 16, 64, 3};
-    b->L[1] = Launch{32, 16, 64, 2};
+    b->L[1] = Launch{32, 32, 64, 2};
     *out = b;
     return FD_OK;
 }

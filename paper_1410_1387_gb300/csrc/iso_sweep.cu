@@ -37,7 +37,12 @@ constexpr long long kWaitLimit = 2000000000LL;
 template <int R, int TX, int TY, int LA, int NBT = 2>
 struct IsoCfg {
     static constexpr int NTX = TX / 4;              // consumer threads per tile row
-    static constexpr int NC = NTX * TY;             // consumer threads
+    // Radius 8 in 32 x 32 tiles (the forward and adjoint sweeps; not the gradient
+    // sweep) keeps its z queues in tensor memory, which frees the registers for
+    // two tile rows per thread: the rows share their y-neighbour reads.
+    static constexpr bool TQ = (R == 8 && TX == 32 && TY == 32 && NBT == 2);
+    static constexpr int RPT = TQ ? 2 : 1;          // tile rows per consumer thread
+    static constexpr int NC = NTX * TY / RPT;       // consumer threads
     static constexpr int NCW = NC / 32;             // consumer warps
     static constexpr int NT = NC + 32;              // + one producer warp
     static constexpr int SW = TX + 2 * R;           // staged row width (floats)
@@ -51,12 +56,12 @@ struct IsoCfg {
     static constexpr int SLOT_B = NBT_ALL * TX * TY;   // floats per ring B plane
     static constexpr int NA = LA + 1;               // ring A slots
     // CTAs per SM the registers are budgeted for
-    static constexpr int MINB = (TX / 4) * TY + 32 <= 160 ? (R >= 8 ? 3 : 4) : 2;
-    // Radius 8 in 32 x 16 tiles keeps its z queue in tensor memory instead of
-    // registers (the forward sweep; the adjoint's injection and gradient forms
-    // keep the register queue): 64 registers freed, four CTAs per SM.
-    static constexpr bool TQ_TILE = (R == 8 && TX == 32 && TY == 16);
-    static constexpr int minb(bool tq) { return tq ? 4 : MINB; }
+    static constexpr int MINB = TQ ? 2 : (NT <= 160 ? (R >= 8 ? 3 : 4) : 2);
+    // Tensor memory per CTA: two rows x 128 columns.  The shared-memory floor keeps
+    // at most two such CTAs on an SM, so their allocations (2 x 256 of the 512
+    // columns) never wait.
+    static constexpr int TMEM_COLS = 256;
+    static constexpr int SMEM_FLOOR = TQ ? 80 * 1024 : 0;
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
@@ -65,6 +70,7 @@ struct IsoCfg {
     static constexpr int SMEM = OFF_GZ;
     static_assert(TX % 4 == 0 && R % 4 == 0, "x alignment");
     static_assert(NC % 32 == 0, "whole consumer warps");
+    static_assert(!TQ || NC == 128, "tensor-memory queues: one consumer warp per lane quarter");
     static_assert((SLOT_A * 4) % 128 == 0 && (SLOT_B * 4) % 128 == 0, "slot alignment");
     static_assert(SW <= 256 && SH <= 256, "TMA box limit");
 };
@@ -108,8 +114,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                                          const int bz, const CUtensorMap *tm_grad = nullptr)
 {
     using C = IsoCfg<R, TX, TY, LA, GRAD ? 3 : 2>;
-    constexpr bool TQ = C::TQ_TILE && !INJ && !GRAD;
-    static_assert(!TQ || (R == 8 && C::NCW == 4), "tensor-memory queue: 16-plane ring, one warp per lane quarter");
+    constexpr bool TQ = C::TQ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *ringA = reinterpret_cast<float *>(smem_raw);
     float *ringB = reinterpret_cast<float *>(smem_raw + C::OFF_B);
@@ -146,7 +151,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
     for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
     if constexpr (TQ) {
         __syncwarp();
-        if (tid < 32) tmem_alloc(sh_tmem, 128);
+        if (tid < 32) tmem_alloc(sh_tmem, C::TMEM_COLS);
         tmem_fence_before_sync();
     }
     __syncthreads();
@@ -207,8 +212,222 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             sh[2] = a_end;
             sh[3] = b_end;
         }
+    } else if constexpr (TQ) {
+        // ------------------------------------------------------------ consumer warps (two rows each)
+        // Thread (tx, tr) owns 4 consecutive x points of tile rows 2 tr and 2 tr + 1.
+        // Their y neighbours overlap, so each staged row above and below is read
+        // once for both: 16 float4 reads per 8 points instead of 32.  Per point the
+        // arithmetic, and its order, is that of the one-row form.
+        const int tx = tid % C::NTX, tr = tid / C::NTX;
+        const int lane = tid & 31;
+        const int gxi = x0 + 4 * tx, gy0 = y0 + 2 * tr;
+        const bool xin = gxi < a.nx;
+        const bool act[2] = {xin && gy0 < a.ny, xin && gy0 + 1 < a.ny};
+        const long long rowoff0 = (long long)gy0 * a.pitch + gxi;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int own = (2 * tr + R) * C::SW + R + 4 * tx;   // row 0's float4 in a ring A slot (row 1: + SW)
+        const int ownb = 2 * tr * TX + 4 * tx;               // row 0's float4 in a ring B tile (row 1: + TX)
+
+        // z queues in my tensor-memory lane: row e's values of planes k - R ..
+        // k + R - 1 in columns 128 e + [0, 128), plane p in slot p mod 16 at 4 s
+        // and again at 64 + 4 s, so that the window of plane k is the contiguous
+        // run of 64 columns from its plane k - R.  Plane k + R enters from ring B.
+        const uint32_t tl = *sh_tmem + ((uint32_t)(32 * (tid / 32)) << 16);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+#pragma unroll
+            for (int m0 = 0; m0 < 2 * R; m0 += 8) {
+                float4 v[8];   // eight loads in flight before their stores
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int p = z0 - R + m0 + m;
+                    v[m] = (act[e] && p >= 0 && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff0 + e * a.pitch)
+                                                          : zero4;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const uint32_t c = tl + 128 * e + 4 * (uint32_t)((z0 - R + m0 + m) & 15);
+                    tmem_st4x2(c, c + 64, v[m]);
+                }
+            }
+        }
+        float4 g4 = zero4;
+        float gyv[2] = {0.f, 0.f};
+        if (xin) g4 = *reinterpret_cast<const float4 *>(a.gx + gxi);
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (act[e]) gyv[e] = a.gy[gy0 + e];
+
+        // tcgen05 loads and stores are warp-collective: every warp takes each
+        // branch as a whole, so the abort flag and each bounded wait are agreed
+        // across the warp.
+        bool ok = true;
+        for (int k = z0; ok && k < z1; ++k) {
+            if (!__all_sync(0xffffffffu, *sh_abort == 0)) {
+                ok = false;
+                break;
+            }
+            const int ub = k - z0, sb = ub % C::NB;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&fullB[sb], (ub / C::NB) & 1, kWaitLimit))) {
+                ok = false;
+                break;
+            }
+            const float *tb = ringB + sb * C::SLOT_B;
+            float4 qin[2], pv[2], kv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                qin[e] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb + e * TX);
+                pv[e] = *reinterpret_cast<const float4 *>(tb + ownb + e * TX);
+                kv[e] = *reinterpret_cast<const float4 *>(tb + TX * TY + ownb + e * TX);
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit))) {
+                ok = false;
+                break;
+            }
+            const float gz = sgz[k - z0];
+            const int sa = (k - z0) % C::NA;
+            const float *t = ringA + sa * C::SLOT_A;
+
+            // x windows: floats [4tx - R, 4tx + 4 + R) of both rows of plane k
+            float xw[2][4 + 2 * R];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float *rw = t + own + e * C::SW - R;
+#pragma unroll
+                for (int m = 0; m < (4 + 2 * R) / 4; ++m) {
+                    const float4 v = *reinterpret_cast<const float4 *>(rw + 4 * m);
+                    xw[e][4 * m + 0] = v.x; xw[e][4 * m + 1] = v.y; xw[e][4 * m + 2] = v.z; xw[e][4 * m + 3] = v.w;
+                }
+            }
+            // centre, then x pairs, per point
+            float2 lo[2], hi[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float acc[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[i] = a.w0 * xw[e][R + i];
+#pragma unroll
+                for (int l = 1; l <= R; ++l)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[i] = fmaf(a.wxy[l], xw[e][R + i + l] + xw[e][R + i - l], acc[i]);
+                lo[e] = make_float2(acc[0], acc[1]);
+                hi[e] = make_float2(acc[2], acc[3]);
+            }
+            auto pair = [&](int e, const float2 w, const float4 &up, const float4 &dn) {
+                lo[e] = __ffma2_rn(w, __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo[e]);
+                hi[e] = __ffma2_rn(w, __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi[e]);
+            };
+            // y pairs: at l, row 0 takes rows (l, -l) and row 1 rows (l + 1, 1 - l),
+            // relative to row 0; rows 0 and 1 themselves are the x windows' centres
+            float4 up0 = make_float4(xw[1][R], xw[1][R + 1], xw[1][R + 2], xw[1][R + 3]);
+            float4 dn1 = make_float4(xw[0][R], xw[0][R + 1], xw[0][R + 2], xw[0][R + 3]);
+#pragma unroll
+            for (int l = 1; l <= R; ++l) {
+                const float4 dn0 = *reinterpret_cast<const float4 *>(t + own - l * C::SW);
+                const float4 up1 = *reinterpret_cast<const float4 *>(t + own + (l + 1) * C::SW);
+                pair(0, a.wxy2[l], up0, dn0);
+                pair(1, a.wxy2[l], up1, dn1);
+                up0 = up1;
+                dn1 = dn0;
+            }
+            // this warp no longer reads plane k from either ring
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&emptyA[sa]);
+                mbar_arrive(&emptyB[sb]);
+            }
+            // z pairs from the window: plane k - R + j at columns w0 + 4 j (+ 128 e)
+            {
+                const uint32_t w0 = tl + 4 * (uint32_t)((k - R) & 15);
+                float4 va0[4], vb0[4], va1[4], vb1[4];
+                __syncwarp();
+                // planes k-4..k-1 and k+1..k+4 of both rows
+                tmem_ld16x4(w0 + 16, w0 + 36, w0 + 144, w0 + 164, va0, vb0, va1, vb1);
+#pragma unroll
+                for (int l = 1; l <= 4; ++l) {
+                    pair(0, a.wz2[l], vb0[l - 1], va0[4 - l]);
+                    pair(1, a.wz2[l], vb1[l - 1], va1[4 - l]);
+                }
+                // planes k-8..k-5 and k+4..k+7; plane k+8 is the entering one
+                tmem_ld16x4(w0, w0 + 48, w0 + 128, w0 + 176, va0, vb0, va1, vb1);
+#pragma unroll
+                for (int l = 5; l <= 8; ++l) {
+                    pair(0, a.wz2[l], l == 8 ? qin[0] : vb0[l - 4], va0[8 - l]);
+                    pair(1, a.wz2[l], l == 8 ? qin[1] : vb1[l - 4], va1[8 - l]);
+                }
+                // plane k + 8 takes the slot of plane k - 8, no longer needed
+                tmem_st4x2(w0, w0 + 64, qin[0]);
+                tmem_st4x2(w0 + 128, w0 + 192, qin[1]);
+            }
+
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!act[e]) continue;
+                const int gyi = gy0 + e;
+                const long long rowoff = rowoff0 + e * a.pitch;
+                const float acc[4] = {lo[e].x, lo[e].y, hi[e].x, hi[e].y};
+                const float gyz = gyv[e] * gz;
+                const float cu[4] = {xw[e][R], xw[e][R + 1], xw[e][R + 2], xw[e][R + 3]};
+                const float pu[4] = {pv[e].x, pv[e].y, pv[e].z, pv[e].w};
+                const float ku[4] = {kv[e].x, kv[e].y, kv[e].z, kv[e].w};
+                const float gu[4] = {g4.x, g4.y, g4.z, g4.w};
+                float o[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float G = gu[i] * gyz;
+                    o[i] = fmaf(ku[i], acc[i], fmaf(2.f, cu[i], -G * pu[i]));
+                }
+                if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len)
+                    o[a.src.sx - gxi] += a.src.tab[n];
+                if (INJ && k == a.inj.rk) {
+                    // lattice of additive sources (the adjoint's receiver residuals)
+                    const int ry = gyi - a.inj.ry0;
+                    const int row = n - a.inj.t0;
+                    if (ry >= 0 && ry % a.inj.rsy == 0 && ry / a.inj.rsy < a.inj.rny && row >= 0 &&
+                        row < a.inj.cap) {
+                        const float *irow = a.inj.trace + (long long)row * a.inj.nrec +
+                                            (long long)(ry / a.inj.rsy) * a.inj.rnx;
+                        for (int i = 0; i < 4; ++i) {
+                            const int rx = gxi + i - a.inj.rx0;
+                            if (gxi + i < a.nx && rx >= 0 && rx % a.inj.rsx == 0 && rx / a.inj.rsx < a.inj.rnx)
+                                o[i] += irow[rx / a.inj.rsx];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o[i] *= gu[i] * gyz;
+
+                float *dst = prev + k * a.plane + rowoff;
+                if (gxi + 3 < a.nx) {
+                    st_cs(dst, make_float4(o[0], o[1], o[2], o[3]));
+                } else {
+                    for (int i = 0; i < 4; ++i)
+                        if (gxi + i < a.nx) dst[i] = o[i];
+                }
+
+                if (a.rec.on && k == a.rec.rk) {
+                    const int ry = gyi - a.rec.ry0;
+                    const int row = n - a.rec.t0;
+                    if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 &&
+                        row < a.rec.cap) {
+                        float *trow = a.rec.trace + (long long)row * a.rec.nrec +
+                                      (long long)(ry / a.rec.rsy) * a.rec.rnx;
+                        for (int i = 0; i < 4; ++i) {
+                            const int rx = gxi + i - a.rec.rx0;
+                            if (gxi + i < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
+                                trow[rx / a.rec.rsx] = o[i];
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok) {
+            *sh_abort = 1;
+            failed = true;
+        }
     } else {
-        // ------------------------------------------------------------ consumer warps
+        // ------------------------------------------------------------ consumer warps (one row each)
         const int tx = tid % C::NTX, ty = tid / C::NTX;
         const int lane = tid & 31;
         const int gxi = x0 + 4 * tx, gyi = y0 + ty;
@@ -218,35 +437,18 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         const int own = (ty + R) * C::SW + R + 4 * tx;   // my float4 in a ring A slot
         const int ownb = ty * TX + 4 * tx;               // my float4 in a ring B tile
 
-        // z queue: q[R + m] = my 4 values of plane k + m, m = -R..R.
-        // Tensor-memory form: only q[0] (plane k + R, entering) is a register; my
-        // values of planes k - R .. k + R - 1 sit in my TMEM lane as a ring of 16
-        // slots of 4 columns, plane p in slot p mod 16, stored twice (columns
-        // 4 s and 64 + 4 s) so that the window of any plane is one contiguous run
-        // of 64 columns starting at its plane k - R.
-        float4 q[TQ ? 1 : 2 * R + 1];
-        uint32_t tq_lane = 0;
+        // z queue: q[R + m] = my 4 values of plane k + m, m = -R..R
+        float4 q[2 * R + 1];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int p = z0 - R + m;
+            q[m] = (act && p >= 0) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
+        }
         bool ok = true;
-        if constexpr (TQ) {
-            tq_lane = *sh_tmem + ((uint32_t)(32 * (tid / 32)) << 16);
-            for (int m = 0; m < 2 * R; ++m) {
-                const int p = z0 - R + m;
-                const float4 v = (act && p >= 0 && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
-                const uint32_t c = tq_lane + 4 * (uint32_t)(p & 15);
-                __syncwarp();
-                tmem_st4x2(c, c + 64, v);
-            }
-        } else {
 #pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const int p = z0 - R + m;
-                q[m] = (act && p >= 0) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
-            }
-#pragma unroll
-            for (int m = 0; m < R; ++m) {
-                const int p = z0 + m;
-                q[R + m] = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
-            }
+        for (int m = 0; m < R; ++m) {
+            const int p = z0 + m;
+            q[R + m] = (act && p < a.nz) ? ld_nc_na(cur + p * a.plane + rowoff) : zero4;
         }
         float4 g4 = zero4;
         float gyv = 0.f;
@@ -255,25 +457,21 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
             gyv = a.gy[gyi];
         }
 
-        // With the tensor-memory queue every warp takes each branch as a whole
-        // (tcgen05 loads and stores are warp-collective), so the abort flag and the
-        // outcome of each bounded wait are agreed across the warp.
-        auto warp_all = [](bool v) { return TQ ? (bool)__all_sync(0xffffffffu, v) : v; };
         for (int k = z0; ok && k < z1; ++k) {
-            if (!warp_all(*sh_abort == 0)) {
+            if (*sh_abort) {
                 ok = false;
                 break;
             }
             const int ub = k - z0, sb = ub % C::NB;
-            if (!warp_all(mbar_wait_bounded(&fullB[sb], (ub / C::NB) & 1, kWaitLimit))) {
+            if (!mbar_wait_bounded(&fullB[sb], (ub / C::NB) & 1, kWaitLimit)) {
                 ok = false;
                 break;
             }
             const float *tb = ringB + sb * C::SLOT_B;
             // my values of plane k + R enter the queue
-            q[TQ ? 0 : 2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
+            q[2 * R] = *reinterpret_cast<const float4 *>(tb + (C::NBT_ALL - 1) * TX * TY + ownb);
             // plane k of u^n with its halo, in ring A
-            if (!warp_all(mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit))) {
+            if (!mbar_wait_bounded(&fullA[ub % C::NA], (ub / C::NA) & 1, kWaitLimit)) {
                 ok = false;
                 break;
             }
@@ -317,26 +515,12 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 mbar_arrive(&emptyA[sa]);
                 mbar_arrive(&emptyB[sb]);
             }
-            auto zpair = [&](int l, const float4 &up, const float4 &dn) {
-                lo = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo);
-                hi = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi);
-            };
-            if constexpr (TQ) {
-                // window of plane k: planes k - 8 + j at columns w0 + 4 j, j = 0..15
-                const uint32_t w0 = tq_lane + 4 * (uint32_t)((k - R) & 15);
-                float4 va[4], vb[4];
-                __syncwarp();
-                tmem_ld16x2(w0 + 16, w0 + 36, va, vb);     // planes k-4..k-1 and k+1..k+4
 #pragma unroll
-                for (int l = 1; l <= 4; ++l) zpair(l, vb[l - 1], va[4 - l]);
-                tmem_ld16x2(w0, w0 + 48, va, vb);          // planes k-8..k-5 and k+4..k+7
-#pragma unroll
-                for (int l = 5; l <= 8; ++l) zpair(l, l == 8 ? q[0] : vb[l - 4], va[8 - l]);
-                // plane k + 8 takes the slot of plane k - 8, no longer needed
-                tmem_st4x2(w0, w0 + 64, q[0]);
-            } else {
-#pragma unroll
-                for (int l = 1; l <= R; ++l) zpair(l, q[R + l], q[R - l]);
+            for (int l = 1; l <= R; ++l) {
+                lo = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(q[R + l].x, q[R + l].y),
+                                                     make_float2(q[R - l].x, q[R - l].y)), lo);
+                hi = __ffma2_rn(a.wz2[l], __fadd2_rn(make_float2(q[R + l].z, q[R + l].w),
+                                                     make_float2(q[R - l].z, q[R - l].w)), hi);
             }
             acc[0] = lo.x;
             acc[1] = lo.y;
@@ -413,10 +597,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                     }
                 }
             }
-            if constexpr (!TQ) {
 #pragma unroll
-                for (int m = 0; m < 2 * R; ++m) q[m] = q[m + 1];
-            }
+            for (int m = 0; m < 2 * R; ++m) q[m] = q[m + 1];
         }
         if (!ok) {
             *sh_abort = 1;
@@ -428,7 +610,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
     const bool any_failed = __syncthreads_or(failed);
     if constexpr (TQ) {
         tmem_fence_after_sync();
-        if (tid < 32) tmem_dealloc(*sh_tmem, 128);
+        if (tid < 32) tmem_dealloc(*sh_tmem, C::TMEM_COLS);
     }
     if (any_failed && tid == C::NC) {
         // A bounded wait gave up somewhere: record it, then wait (bounded) for the
@@ -449,8 +631,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 
 
 template <int R, int TX, int TY, int LA, bool INJ>
-__global__ void __launch_bounds__((TX / 4) * TY + 32,
-                                  (IsoCfg<R, TX, TY, LA>::minb(IsoCfg<R, TX, TY, LA>::TQ_TILE && !INJ)))
+__global__ void __launch_bounds__(IsoCfg<R, TX, TY, LA>::NT, IsoCfg<R, TX, TY, LA>::MINB)
     iso_sweep_kernel(const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_prev,
                      const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_ctile,
                      const __grid_constant__ IsoArgs a)
@@ -468,7 +649,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32,
 // of these launches replays without per-step arguments.  Shots that reached
 // their last step skip their items.
 template <int R, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::minb(IsoCfg<R, TX, TY, LA>::TQ_TILE)))
+__global__ void __launch_bounds__(IsoCfg<R, TX, TY, LA>::NT, IsoCfg<R, TX, TY, LA>::MINB)
     iso_batch_kernel(const int4 *__restrict__ items, const BatchShot *__restrict__ shots)
 {
     using C = IsoCfg<R, TX, TY, LA>;
@@ -490,11 +671,13 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA>::mi
 
 // ---------------------------------------------------------------------------
 
+constexpr int cmax(int x, int y) { return x > y ? x : y; }
+
 template <int R, int TX, int TY, int LA, bool INJ>
 static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t s)
 {
     using C = IsoCfg<R, TX, TY, LA>;
-    constexpr int smem_max = C::SMEM + 4 * kMaxChunk;
+    constexpr int smem_max = cmax(C::SMEM + 4 * kMaxChunk, C::SMEM_FLOOR);
     static bool attr_set[64] = {};   // per device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -507,7 +690,7 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
     IsoArgs a = a0;
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
-    const int smem = C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4);
+    const int smem = cmax(C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4), C::SMEM_FLOOR);
     iso_sweep_kernel<R, TX, TY, LA, INJ><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, tm.cur_tile, a);
     return cudaGetLastError();
 }
@@ -522,7 +705,7 @@ template <int R, int TX, int TY, int LA>
 static cudaError_t launch_b(const int4 *items, int nitems, const BatchShot *shots, int max_zchunk, cudaStream_t s)
 {
     using C = IsoCfg<R, TX, TY, LA>;
-    constexpr int smem = C::SMEM + 4 * kMaxChunk + (int)sizeof(IsoArgs);
+    constexpr int smem = cmax(C::SMEM + 4 * kMaxChunk + (int)sizeof(IsoArgs), C::SMEM_FLOOR);
     (void)max_zchunk;
     static bool attr_set[64] = {};   // per device
     int dev = 0;
@@ -542,7 +725,7 @@ static cudaError_t launch_b(const int4 *items, int nitems, const BatchShot *shot
 // pipeline over a = u^n, with z, kappa and the gradient in ring B.  It does not
 // advance the grid's time index.
 template <int R, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, (IsoCfg<R, TX, TY, LA, 3>::MINB))
+__global__ void __launch_bounds__(IsoCfg<R, TX, TY, LA, 3>::NT, IsoCfg<R, TX, TY, LA, 3>::MINB)
     iso_grad_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_z,
                     const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_grad,
                     const __grid_constant__ CUtensorMap tm_atile, const __grid_constant__ IsoArgs a)
@@ -575,7 +758,13 @@ static cudaError_t launch_g(const IsoMaps &tm, const CUtensorMap &tm_grad, const
 
 Launch iso_grad_launch(int R, int nx, int ny, int nz)
 {
-    return iso_default_launch(R, nx, ny, nz);
+    Launch L = iso_default_launch(R, nx, ny, nz);
+    if (R == 8) {
+        // the gradient sweep keeps the register queue: three CTAs of 32 x 16 per SM
+        L.ty = 16;
+        L.zchunk = default_zchunk(L, nx, ny, nz, 4096);
+    }
+    return L;
 }
 
 cudaError_t launch_iso_grad(int R, const Launch &L, const IsoMaps &tm, const CUtensorMap &tm_grad, const IsoArgs &a,
@@ -596,7 +785,8 @@ cudaError_t launch_iso_grad(int R, const Launch &L, const IsoMaps &tm, const CUt
     X(4, 32, 16, 3)       \
     X(8, 64, 8, 2)        \
     X(8, 64, 8, 3)        \
-    X(8, 32, 16, 2)
+    X(8, 32, 16, 2)       \
+    X(8, 32, 32, 2)
 
 cudaError_t launch_iso(int R, const Launch &L, const IsoMaps &tm, const IsoArgs &a, cudaStream_t s)
 {
@@ -636,11 +826,11 @@ Launch iso_default_launch(int R, int nx, int ny, int nz)
         L.lookahead = 3;
         L.zchunk = default_zchunk(L, nx, ny, nz);
     } else {
-        // three CTAs per SM: about 4096 CTAs make several waves with a short tail
+        // two CTAs of 32 x 32 per SM (z queues in tensor memory, two rows per thread)
         L.tx = 32;
-        L.ty = 16;
+        L.ty = 32;
         L.lookahead = 2;
-        L.zchunk = default_zchunk(L, nx, ny, nz, 4096);
+        L.zchunk = default_zchunk(L, nx, ny, nz, 2048);
     }
     return L;
 }

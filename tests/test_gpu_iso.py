@@ -181,7 +181,7 @@ def test_graph_and_tiles_are_bitwise_identical(fd):
     np.testing.assert_array_equal(t0, t2)
 
 
-@pytest.mark.parametrize("launch", [(64, 8, 17, 3), (32, 16, 9, 2)])
+@pytest.mark.parametrize("launch", [(64, 8, 17, 3), (32, 16, 9, 2), (32, 32, 9, 2)])
 def test_radius8_tiles_are_bitwise_identical(fd, O, launch):
     """Radius 8 in other tiles, z chunks and lookaheads, ragged in x, y and z:
     the same values bit for bit, and the oracle's within tolerance."""
