@@ -824,13 +824,13 @@ Launch iso_default_launch(int R, int nx, int ny, int nz)
         L.tx = 64;
         L.ty = 16;
         L.lookahead = 3;
-        L.zchunk = default_zchunk(L, nx, ny, nz);
+        L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<4, 64, 16, 3>::MINB, 2 * R);
     } else {
         // two CTAs of 32 x 32 per SM (z queues in tensor memory, two rows per thread)
         L.tx = 32;
         L.ty = 32;
         L.lookahead = 2;
-        L.zchunk = default_zchunk(L, nx, ny, nz, 2048);
+        L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<8, 32, 32, 2>::MINB, 2 * R);
     }
     return L;
 }

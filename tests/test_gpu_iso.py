@@ -315,7 +315,7 @@ def test_bounded_wait_reports_timeout(fd, O, R):
     with pytest.raises(fd.FdError) as e:
         fd.fd_debug_skip_copy(g.h, 40)
     assert e.value.code == fd.FD_ERR_INVALID_ARG
-    fd.fd_debug_skip_copy(g.h, 6)         # CTA (0,0,0)'s z chunk is planes 0..31
+    fd.fd_debug_skip_copy(g.h, 6)         # in the z chunk of CTA (0,0,0), which starts at plane 0
     t0 = time.perf_counter()
     g.run(1)
     with pytest.raises(fd.FdError) as e:

@@ -1,0 +1,59 @@
+"""Host logic of the default launch shape (no GPU): the wave-fitted z chunk of
+fd_internal.h, compiled with the host compiler against the CUDA headers.  It
+must end for every grid (an nz of 1 once made the search loop forever), stay
+within [min(32, nz), 128] and nz, and at 512^3 on 152 SMs x 2 CTAs pick 7
+chunks of 74 planes."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PROGRAM = r"""
+#include "fd_internal.h"
+#include <cstdio>
+int main()
+{
+    const fdk::Launch shapes[2] = {{64, 16, 0, 3}, {32, 32, 0, 2}};
+    const int xs[] = {1, 7, 64, 512, 200003}, ys[] = {1, 33, 512, 70001};
+    long bad = 0;
+    for (int nz = 1; nz <= 3000; ++nz)
+        for (int nx : xs)
+            for (int ny : ys)
+                for (const fdk::Launch &L : shapes) {
+                    const int z = fdk::wave_zchunk(L, nx, ny, nz, 304, 8);
+                    const int lo = nz < 32 ? nz : 32;
+                    if (z < lo || z > nz || z > 128) ++bad;
+                }
+    printf("%ld %d %d %d %d\n", bad, fdk::wave_zchunk(shapes[0], 512, 512, 512, 304, 8),
+           fdk::wave_zchunk(shapes[1], 512, 512, 512, 304, 16), fdk::wave_zchunk(shapes[0], 1, 1, 1, 304, 8),
+           fdk::wave_zchunk(shapes[0], 320, 320, 320, 304, 8));
+    return 0;
+}
+"""
+
+
+def _cuda_include():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+
+
+def test_wave_zchunk_ends_and_stays_in_bounds(tmp_path):
+    inc = _cuda_include()
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")) or not shutil.which("g++"):
+        pytest.skip("no CUDA headers or host compiler")
+    src = tmp_path / "wz.cpp"
+    src.write_text(PROGRAM)
+    exe = tmp_path / "wz"
+    b = subprocess.run(["g++", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_1410_1387_gb300", "csrc"),
+                        "-I", inc, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert b.returncode == 0, b.stderr[-2000:]
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0
+    bad, r4, r8, one, c320 = map(int, r.stdout.split())
+    assert bad == 0
+    assert r4 == 74 and r8 == 74          # 7 chunks: 1792 CTAs = 5.9 waves of 304
+    assert one == 1
+    assert c320 == 107                    # 3 chunks of 5 x 20 tiles: 300 CTAs, one wave
