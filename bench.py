@@ -231,10 +231,20 @@ def cpu_model():
 # traffic recorded by ncu (profiles/), valid while the kernel source is unchanged
 # ---------------------------------------------------------------------------
 
+def _code_only(src: str) -> str:
+    """C++ source without its comments and with whitespace runs collapsed: what
+    the compiler sees (string literals here hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_hash(kernel: str) -> str:
+    """Hash of the code (comments and layout aside) of a kernel's source file and
+    the headers it shares."""
     h = hashlib.sha256()
     for f in (KERNEL_SRC[kernel], "ptx.cuh", "fd_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1410_1387_gb300", "csrc", f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, "paper_1410_1387_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -15,7 +15,9 @@
 //   * each consumer thread owns 4 consecutive x points (one float4) of one row
 //     and keeps their 2R+1 z neighbours in registers (plane k + R enters from
 //     ring B); x and y neighbours come from the staged plane (x as 1 + R/2
-//     aligned float4 reads, y as 2R);
+//     aligned float4 reads, y as 2R).  Radius 8 in 32 x 32 tiles keeps the z
+//     neighbours in tensor memory instead, and each thread takes two adjacent
+//     rows, which share their y reads;
 //   * u^{n+1} is written in place over u^{n-1} with 128-bit evict-first stores
 //     (each point's older value was staged before any thread writes it);
 //   * the damping is applied in its deferred form G (2u - G u_prev + kappa Lu + s),
@@ -50,8 +52,8 @@ struct IsoCfg {
     static constexpr int SLOT_A = SW * SH;          // floats per u^n plane
     // Each plane's own values for the z queue arrive as one more ring B tile
     // (u^n of plane k + R), so ring A holds only the LA + 1 planes in flight
-    // rather than R planes ahead: small enough for three (radius 8) or four
-    // (radius 4) CTAs of 160 threads per SM.
+    // rather than R planes ahead: small enough for three radius-8 or four
+    // radius-4 CTAs of 160 threads per SM in the register form.
     static constexpr int NBT_ALL = NBT + 1;
     static constexpr int SLOT_B = NBT_ALL * TX * TY;   // floats per ring B plane
     static constexpr int NA = LA + 1;               // ring A slots

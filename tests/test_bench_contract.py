@@ -31,3 +31,13 @@ def test_l2_note_tracks_the_input_size():
     import bench
     assert bench.l2_note(3 * 4 * 512 ** 3).startswith("no flush")
     assert "may stay" in bench.l2_note(3 * 4 * 64 ** 3)
+
+
+def test_kernel_hash_ignores_comments_and_layout():
+    """The recorded DRAM traffic stays valid across comment-only edits of the
+    kernel source, and no longer once the code changes."""
+    import bench
+    a = "int f(int x) { // doubles\n  return 2 * x; /* the\n factor */ }\n"
+    b = "int f(int x) {\n\n    return 2 * x;   }"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench._code_only(a) == bench._code_only(b) != bench._code_only(c)
