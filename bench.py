@@ -46,6 +46,7 @@ WORKLOADS = {
     "vti512": dict(mode="vti", R=12, bytes_per_pt=36, kernel="vti_sweep_kernel"),
 }
 KERNEL_SRC = {"iso_sweep_kernel": "iso_sweep.cu", "vti_sweep_kernel": "vti_sweep.cu"}
+KERNEL_HEADERS = {"iso_sweep_kernel": ("tmem.cuh", "launch_shape.h")}   # besides ptx.cuh and fd_internal.h
 
 
 def parse():
@@ -243,7 +244,7 @@ def kernel_hash(kernel: str) -> str:
     """Hash of the code (comments and layout aside) of a kernel's source file and
     the headers it shares."""
     h = hashlib.sha256()
-    for f in (KERNEL_SRC[kernel], "ptx.cuh", "fd_internal.h"):
+    for f in (KERNEL_SRC[kernel], "ptx.cuh", "fd_internal.h") + KERNEL_HEADERS.get(kernel, ()):
         h.update(_code_only(open(os.path.join(ROOT, "paper_1410_1387_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:12]
 

@@ -27,7 +27,9 @@
 // write u^{n+1}).  All waits are bounded (about 1 s); a CTA that gives up sets
 // an error flag, drains its copies in flight and exits.
 #include "fd_internal.h"
+#include "launch_shape.h"
 #include "ptx.cuh"
+#include "tmem.cuh"
 
 namespace fdk {
 
@@ -58,12 +60,12 @@ struct IsoCfg {
     static constexpr int SLOT_B = NBT_ALL * TX * TY;   // floats per ring B plane
     static constexpr int NA = LA + 1;               // ring A slots
     // CTAs per SM the registers are budgeted for
-    static constexpr int MINB = TQ ? 2 : (NT <= 160 ? (R >= 8 ? 3 : 4) : 2);
-    // Tensor memory per CTA: two rows x 128 columns.  The shared-memory floor keeps
-    // at most two such CTAs on an SM, so their allocations (2 x 256 of the 512
-    // columns) never wait.
-    static constexpr int TMEM_COLS = 256;
-    static constexpr int SMEM_FLOOR = TQ ? 80 * 1024 : 0;
+    static constexpr int MINB = TQ ? 3 : (NT <= 160 ? (R >= 8 ? 3 : 4) : 2);
+    // Tensor memory per CTA: two rows x 64 columns.  Shared memory (over 57 KB a
+    // CTA) keeps at most three such CTAs on an SM, so their allocations (3 x 128
+    // of the 512 columns) never wait.
+    static constexpr int TMEM_COLS = 128;
+    static constexpr int SMEM_FLOOR = 0;
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
@@ -231,9 +233,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         const int ownb = 2 * tr * TX + 4 * tx;               // row 0's float4 in a ring B tile (row 1: + TX)
 
         // z queues in my tensor-memory lane: row e's values of planes k - R ..
-        // k + R - 1 in columns 128 e + [0, 128), plane p in slot p mod 16 at 4 s
-        // and again at 64 + 4 s, so that the window of plane k is the contiguous
-        // run of 64 columns from its plane k - R.  Plane k + R enters from ring B.
+        // k + R - 1 in columns 64 e + [0, 64), plane p in slot p mod 16 at
+        // 4 s.  Plane k + R enters from ring B.
         const uint32_t tl = *sh_tmem + ((uint32_t)(32 * (tid / 32)) << 16);
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -249,8 +250,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 __syncwarp();
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
-                    const uint32_t c = tl + 128 * e + 4 * (uint32_t)((z0 - R + m0 + m) & 15);
-                    tmem_st4x2(c, c + 64, v[m]);
+                    tmem_st4(tl + 64 * e + 4 * (uint32_t)((z0 - R + m0 + m) & 15), v[m]);
                 }
             }
         }
@@ -339,28 +339,33 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 mbar_arrive(&emptyA[sa]);
                 mbar_arrive(&emptyB[sb]);
             }
-            // z pairs from the window: plane k - R + j at columns w0 + 4 j (+ 128 e)
+            // z pairs from the tensor-memory queues
             {
-                const uint32_t w0 = tl + 4 * (uint32_t)((k - R) & 15);
-                float4 va0[4], vb0[4], va1[4], vb1[4];
-                __syncwarp();
-                // planes k-4..k-1 and k+1..k+4 of both rows
-                tmem_ld16x4(w0 + 16, w0 + 36, w0 + 144, w0 + 164, va0, vb0, va1, vb1);
+                // per row, pairs l = 1..4 then 5..8: planes k + l and k - l from their
+                // slots (plane k + 8 is the entering one; its slot still holds k - 8)
 #pragma unroll
-                for (int l = 1; l <= 4; ++l) {
-                    pair(0, a.wz2[l], vb0[l - 1], va0[4 - l]);
-                    pair(1, a.wz2[l], vb1[l - 1], va1[4 - l]);
-                }
-                // planes k-8..k-5 and k+4..k+7; plane k+8 is the entering one
-                tmem_ld16x4(w0, w0 + 48, w0 + 128, w0 + 176, va0, vb0, va1, vb1);
+                for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int l = 5; l <= 8; ++l) {
-                    pair(0, a.wz2[l], l == 8 ? qin[0] : vb0[l - 4], va0[8 - l]);
-                    pair(1, a.wz2[l], l == 8 ? qin[1] : vb1[l - 4], va1[8 - l]);
-                }
+                    for (int e = 0; e < 2; ++e) {
+                        uint32_t c[8];
+                        float4 v[8];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int l = 4 * h + 1 + i;
+                            c[2 * i] = tl + 64 * e + 4 * (uint32_t)((k + l) & 15);
+                            c[2 * i + 1] = tl + 64 * e + 4 * (uint32_t)((k - l) & 15);
+                        }
+                        __syncwarp();
+                        tmem_ld4x8(c, v);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int l = 4 * h + 1 + i;
+                            pair(e, a.wz2[l], l == 8 ? qin[e] : v[2 * i], v[2 * i + 1]);
+                        }
+                    }
                 // plane k + 8 takes the slot of plane k - 8, no longer needed
-                tmem_st4x2(w0, w0 + 64, qin[0]);
-                tmem_st4x2(w0 + 128, w0 + 192, qin[1]);
+                const uint32_t cs = tl + 4 * (uint32_t)((k + R) & 15);
+                tmem_st4_2(cs, qin[0], cs + 64, qin[1]);
             }
 
 #pragma unroll

@@ -125,84 +125,4 @@ __device__ __forceinline__ void st_cs(float *p, float4 v)
                  : "memory");
 }
 
-// ---------------------------------------------------------------- tensor memory
-// TMEM (tcgen05) as private per-thread storage: with the 32x32b shapes thread t
-// of warp w (w < 4 within its warpgroup) reads and writes lane 32 w + t, one
-// 32-bit value per column.  Allocation is by whole columns for all 128 lanes.
-
-// Allocates ncols columns (a power of two >= 32); one full warp executes it and
-// the column address lands in *dst (shared memory).
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// Orders tensor-memory accesses around a thread barrier.
-__device__ __forceinline__ void tmem_fence_before_sync()
-{
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_fence_after_sync()
-{
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Stores v at columns [c, c + 4) and [c2, c2 + 4) of this thread's lane and
-// waits for both stores to complete.
-__device__ __forceinline__ void tmem_st4x2(uint32_t c, uint32_t c2, float4 v)
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%2, %3, %4, %5};\n\t"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%2, %3, %4, %5};\n\t"
-        "tcgen05.wait::st.sync.aligned;" ::"r"(c),
-        "r"(c2), "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
-        "r"(__float_as_uint(v.w))
-        : "memory");
-}
-
-// Loads 16 columns from each of c0..c3 in this thread's lane (four float4 per
-// address) and waits for them: the values are defined only once the asm ends.
-__device__ __forceinline__ void tmem_ld16x4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, float4 (&v0)[4],
-                                            float4 (&v1)[4], float4 (&v2)[4], float4 (&v3)[4])
-{
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, "
-        "%8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, "
-        "%24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, "
-        "%40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, "
-        "%56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-    float4 *v[4] = {v0, v1, v2, v3};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int b = 16 * q + 4 * i;
-            v[q][i] = make_float4(__uint_as_float(r[b]), __uint_as_float(r[b + 1]), __uint_as_float(r[b + 2]),
-                                  __uint_as_float(r[b + 3]));
-        }
-}
-
 }  // namespace fdk

@@ -1,0 +1,88 @@
+// Tensor memory (tcgen05) as private per-thread storage, in inline PTX.
+#pragma once
+#include <stdint.h>
+
+#include "ptx.cuh"
+
+namespace fdk {
+
+// TMEM (tcgen05) as private per-thread storage: with the 32x32b shapes thread t
+// of warp w (w < 4 within its warpgroup) reads and writes lane 32 w + t, one
+// 32-bit value per column.  Allocation is by whole columns for all 128 lanes.
+
+// Allocates ncols columns (a power of two >= 32); one full warp executes it and
+// the column address lands in *dst (shared memory).
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Orders tensor-memory accesses around a thread barrier.
+__device__ __forceinline__ void tmem_fence_before_sync()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Stores v at columns [c, c + 4) of this thread's lane and waits for it.
+__device__ __forceinline__ void tmem_st4(uint32_t c, float4 v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(c),
+        "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)), "r"(__float_as_uint(v.w))
+        : "memory");
+}
+
+// Stores v0 at columns [c0, c0 + 4) and v1 at [c1, c1 + 4) and waits for both.
+__device__ __forceinline__ void tmem_st4_2(uint32_t c0, float4 v0, uint32_t c1, float4 v1)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%2, %3, %4, %5};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%6, %7, %8, %9};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(c0),
+        "r"(c1), "r"(__float_as_uint(v0.x)), "r"(__float_as_uint(v0.y)), "r"(__float_as_uint(v0.z)),
+        "r"(__float_as_uint(v0.w)), "r"(__float_as_uint(v1.x)), "r"(__float_as_uint(v1.y)), "r"(__float_as_uint(v1.z)),
+        "r"(__float_as_uint(v1.w))
+        : "memory");
+}
+
+// Loads 4 columns from each of c[0..7] in this thread's lane (one float4 per
+// address) and waits for them: the values are defined only once the asm ends.
+__device__ __forceinline__ void tmem_ld4x8(const uint32_t (&c)[8], float4 (&v)[8])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%35];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%36];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20, %21, %22, %23}, [%37];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%38];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28, %29, %30, %31}, [%39];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(c[5]), "r"(c[6]), "r"(c[7])
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]), __uint_as_float(r[4 * i + 2]),
+                           __uint_as_float(r[4 * i + 3]));
+}
+
+}  // namespace fdk

@@ -1,8 +1,8 @@
 """Host logic of the default launch shape (no GPU): the wave-fitted z chunk of
-fd_internal.h, compiled with the host compiler against the CUDA headers.  It
+launch_shape.h, compiled with the host compiler against the CUDA headers.  It
 must end for every grid (an nz of 1 once made the search loop forever), stay
-within [min(32, nz), 128] and nz, and at 512^3 on 152 SMs x 2 CTAs pick 7
-chunks of 74 planes."""
+within [min(32, nz), 96] and nz, and at 512^3 pick 7 chunks of 74 planes on
+152 SMs x 2 CTAs (radius 4) and x 3 CTAs (radius 8)."""
 import os
 import shutil
 import subprocess
@@ -12,7 +12,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 PROGRAM = r"""
-#include "fd_internal.h"
+#include "launch_shape.h"
 #include <cstdio>
 int main()
 {
@@ -25,10 +25,10 @@ int main()
                 for (const fdk::Launch &L : shapes) {
                     const int z = fdk::wave_zchunk(L, nx, ny, nz, 304, 8);
                     const int lo = nz < 32 ? nz : 32;
-                    if (z < lo || z > nz || z > 128) ++bad;
+                    if (z < lo || z > nz || z > 96) ++bad;
                 }
     printf("%ld %d %d %d %d\n", bad, fdk::wave_zchunk(shapes[0], 512, 512, 512, 304, 8),
-           fdk::wave_zchunk(shapes[1], 512, 512, 512, 304, 16), fdk::wave_zchunk(shapes[0], 1, 1, 1, 304, 8),
+           fdk::wave_zchunk(shapes[1], 512, 512, 512, 456, 16), fdk::wave_zchunk(shapes[0], 1, 1, 1, 304, 8),
            fdk::wave_zchunk(shapes[0], 320, 320, 320, 304, 8));
     return 0;
 }
@@ -54,6 +54,6 @@ def test_wave_zchunk_ends_and_stays_in_bounds(tmp_path):
     assert r.returncode == 0
     bad, r4, r8, one, c320 = map(int, r.stdout.split())
     assert bad == 0
-    assert r4 == 74 and r8 == 74          # 7 chunks: 1792 CTAs = 5.9 waves of 304
+    assert r4 == 74 and r8 == 74          # 7 chunks: 1792 CTAs, 5.9 waves of 304 or 3.9 of 456
     assert one == 1
-    assert c320 == 107                    # 3 chunks of 5 x 20 tiles: 300 CTAs, one wave
+    assert c320 == 54                     # 6 chunks of 5 x 20 tiles: 600 CTAs, two waves of 304
