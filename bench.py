@@ -488,14 +488,18 @@ def run_serve(args):
     torch.cuda.set_device(0)
     reqs = synth.poisson_requests(args.requests, rate=args.rate, seed=77)
     pts = sum(r.n ** 3 * r.steps for r in reqs)
-    server = serve.ShotServer(int(args.budget_gb * 2 ** 30), steps_per_iter=25)
-    t0 = time.perf_counter()
-    res_s = server.serve(reqs, realtime=True)
-    wall_s = time.perf_counter() - t0
-    torch.cuda.empty_cache()
-    t0 = time.perf_counter()
-    res_f = serve.fifo_loop(reqs, realtime=True)
-    wall_f = time.perf_counter() - t0
+    # each form twice, alternating, and the second pass of each reported: a process's
+    # first pass pays one-time costs (the server's first stream: ~10 % of its rate)
+    for _ in range(2):
+        server = serve.ShotServer(int(args.budget_gb * 2 ** 30), steps_per_iter=25)
+        t0 = time.perf_counter()
+        res_s = server.serve(reqs, realtime=True)
+        wall_s = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        res_f = serve.fifo_loop(reqs, realtime=True)
+        wall_f = time.perf_counter() - t0
+        torch.cuda.empty_cache()
     s, f = serve.summary(res_s, wall_s), serve.summary(res_f, wall_f)
     line = {
         "metric": METRIC, "value": s["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "steps": None,
@@ -503,7 +507,7 @@ def run_serve(args):
         "data": "synthetic", "impl": "ours",
         "config": {"workload": "serve_poisson", "requests": len(reqs), "rate_per_s": args.rate,
                    "grids": "cubic, n ~ U{128..400}", "steps": "U{500..2000}", "radius": "4 or 8",
-                   "budget_gb": args.budget_gb, "steps_per_iter": 25,
+                   "budget_gb": args.budget_gb, "steps_per_iter": 25, "passes": "2 of each, second reported",
                    "max_resident_points": server.max_points,
                    "offered_points_per_s": pts / max(r.arrival for r in reqs)},
         "served": s, "fifo_loop": f, "max_resident": server.max_resident,
