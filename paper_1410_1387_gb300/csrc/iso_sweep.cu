@@ -103,6 +103,66 @@ __device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_
     return *sh_n;
 }
 
+// The update of one thread's 4 points of plane k in row gyi (Eq. 3 with the
+// damping in its deferred form, G = gx * gy * gz), with the source, the
+// injection lattice (INJ) and the receivers; u^{n+1} is written over u^{n-1}.
+// acc holds L u^n (the stencil sum), cu u^n, pv u^{n-1}, kv kappa, g4 the x
+// damping factors and gyz = gy * gz.
+template <bool INJ>
+__device__ __forceinline__ void update_row(const IsoArgs &a, float *prev, const int n, const int k, const int gxi,
+                                           const int gyi, const long long rowoff, const float (&acc)[4],
+                                           const float (&cu)[4], const float4 pv, const float4 kv, const float4 g4,
+                                           const float gyz)
+{
+    const float pu[4] = {pv.x, pv.y, pv.z, pv.w};
+    const float ku[4] = {kv.x, kv.y, kv.z, kv.w};
+    const float gu[4] = {g4.x, g4.y, g4.z, g4.w};
+    float o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float G = gu[e] * gyz;
+        o[e] = fmaf(ku[e], acc[e], fmaf(2.f, cu[e], -G * pu[e]));
+    }
+    if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len)
+        o[a.src.sx - gxi] += a.src.tab[n];
+    if (INJ && k == a.inj.rk) {
+        // lattice of additive sources (the adjoint's receiver residuals)
+        const int ry = gyi - a.inj.ry0;
+        const int row = n - a.inj.t0;
+        if (ry >= 0 && ry % a.inj.rsy == 0 && ry / a.inj.rsy < a.inj.rny && row >= 0 && row < a.inj.cap) {
+            const float *irow = a.inj.trace + (long long)row * a.inj.nrec + (long long)(ry / a.inj.rsy) * a.inj.rnx;
+            for (int e = 0; e < 4; ++e) {
+                const int rx = gxi + e - a.inj.rx0;
+                if (gxi + e < a.nx && rx >= 0 && rx % a.inj.rsx == 0 && rx / a.inj.rsx < a.inj.rnx)
+                    o[e] += irow[rx / a.inj.rsx];
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] *= gu[e] * gyz;
+
+    float *dst = prev + k * a.plane + rowoff;
+    if (gxi + 3 < a.nx) {
+        st_cs(dst, make_float4(o[0], o[1], o[2], o[3]));
+    } else {
+        for (int e = 0; e < 4; ++e)
+            if (gxi + e < a.nx) dst[e] = o[e];
+    }
+
+    if (a.rec.on && k == a.rec.rk) {
+        const int ry = gyi - a.rec.ry0;
+        const int row = n - a.rec.t0;
+        if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 && row < a.rec.cap) {
+            float *trow = a.rec.trace + (long long)row * a.rec.nrec + (long long)(ry / a.rec.rsy) * a.rec.rnx;
+            for (int e = 0; e < 4; ++e) {
+                const int rx = gxi + e - a.rec.rx0;
+                if (gxi + e < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
+                    trow[rx / a.rec.rsx] = o[e];
+            }
+        }
+    }
+}
+
 // One CTA's work: tile (bx, by), z chunk bz, of the step u^n -> u^{n+1}.
 // tm_cur maps u^n with the halo box (ring A), tm_ctile u^n with the tile box
 // (the z-queue entries in ring B), tm_prev and tm_kappa the other ring B tiles.
@@ -371,62 +431,10 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 if (!act[e]) continue;
-                const int gyi = gy0 + e;
-                const long long rowoff = rowoff0 + e * a.pitch;
                 const float acc[4] = {lo[e].x, lo[e].y, hi[e].x, hi[e].y};
-                const float gyz = gyv[e] * gz;
                 const float cu[4] = {xw[e][R], xw[e][R + 1], xw[e][R + 2], xw[e][R + 3]};
-                const float pu[4] = {pv[e].x, pv[e].y, pv[e].z, pv[e].w};
-                const float ku[4] = {kv[e].x, kv[e].y, kv[e].z, kv[e].w};
-                const float gu[4] = {g4.x, g4.y, g4.z, g4.w};
-                float o[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float G = gu[i] * gyz;
-                    o[i] = fmaf(ku[i], acc[i], fmaf(2.f, cu[i], -G * pu[i]));
-                }
-                if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len)
-                    o[a.src.sx - gxi] += a.src.tab[n];
-                if (INJ && k == a.inj.rk) {
-                    // lattice of additive sources (the adjoint's receiver residuals)
-                    const int ry = gyi - a.inj.ry0;
-                    const int row = n - a.inj.t0;
-                    if (ry >= 0 && ry % a.inj.rsy == 0 && ry / a.inj.rsy < a.inj.rny && row >= 0 &&
-                        row < a.inj.cap) {
-                        const float *irow = a.inj.trace + (long long)row * a.inj.nrec +
-                                            (long long)(ry / a.inj.rsy) * a.inj.rnx;
-                        for (int i = 0; i < 4; ++i) {
-                            const int rx = gxi + i - a.inj.rx0;
-                            if (gxi + i < a.nx && rx >= 0 && rx % a.inj.rsx == 0 && rx / a.inj.rsx < a.inj.rnx)
-                                o[i] += irow[rx / a.inj.rsx];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) o[i] *= gu[i] * gyz;
-
-                float *dst = prev + k * a.plane + rowoff;
-                if (gxi + 3 < a.nx) {
-                    st_cs(dst, make_float4(o[0], o[1], o[2], o[3]));
-                } else {
-                    for (int i = 0; i < 4; ++i)
-                        if (gxi + i < a.nx) dst[i] = o[i];
-                }
-
-                if (a.rec.on && k == a.rec.rk) {
-                    const int ry = gyi - a.rec.ry0;
-                    const int row = n - a.rec.t0;
-                    if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 &&
-                        row < a.rec.cap) {
-                        float *trow = a.rec.trace + (long long)row * a.rec.nrec +
-                                      (long long)(ry / a.rec.rsy) * a.rec.rnx;
-                        for (int i = 0; i < 4; ++i) {
-                            const int rx = gxi + i - a.rec.rx0;
-                            if (gxi + i < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
-                                trow[rx / a.rec.rsx] = o[i];
-                        }
-                    }
-                }
+                update_row<INJ>(a, prev, n, k, gxi, gy0 + e, rowoff0 + e * a.pitch, acc, cu, pv[e], kv[e], g4,
+                                gyv[e] * gz);
             }
         }
         if (!ok) {
@@ -548,61 +556,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                         if (gxi + e < a.nx) dst[e] = o[e];
                 }
             } else if (act) {
-                const float gyz = gyv * gz;
                 const float cu[4] = {xw[R], xw[R + 1], xw[R + 2], xw[R + 3]};
-                const float pu[4] = {pv.x, pv.y, pv.z, pv.w};
-                const float ku[4] = {kv.x, kv.y, kv.z, kv.w};
-                const float gu[4] = {g4.x, g4.y, g4.z, g4.w};
-                float o[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float G = gu[e] * gyz;
-                    o[e] = fmaf(ku[e], acc[e], fmaf(2.f, cu[e], -G * pu[e]));
-                }
-                if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 &&
-                    n < a.src.len)
-                    o[a.src.sx - gxi] += a.src.tab[n];
-                if (INJ && k == a.inj.rk) {
-                    // lattice of additive sources (the adjoint's receiver residuals)
-                    const int ry = gyi - a.inj.ry0;
-                    const int row = n - a.inj.t0;
-                    if (ry >= 0 && ry % a.inj.rsy == 0 && ry / a.inj.rsy < a.inj.rny && row >= 0 &&
-                        row < a.inj.cap) {
-                        const float *irow = a.inj.trace + (long long)row * a.inj.nrec +
-                                            (long long)(ry / a.inj.rsy) * a.inj.rnx;
-                        for (int e = 0; e < 4; ++e) {
-                            const int rx = gxi + e - a.inj.rx0;
-                            if (gxi + e < a.nx && rx >= 0 && rx % a.inj.rsx == 0 && rx / a.inj.rsx < a.inj.rnx)
-                                o[e] += irow[rx / a.inj.rsx];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) o[e] *= gu[e] * gyz;
-
-                float *dst = prev + k * a.plane + rowoff;
-                if (gxi + 3 < a.nx) {
-                    st_cs(dst, make_float4(o[0], o[1], o[2], o[3]));
-                } else {
-                    for (int e = 0; e < 4; ++e)
-                        if (gxi + e < a.nx) dst[e] = o[e];
-                }
-
-                if (a.rec.on && k == a.rec.rk) {
-                    const int ry = gyi - a.rec.ry0;
-                    const int row = n - a.rec.t0;
-                    if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 &&
-                        row < a.rec.cap) {
-                        float *trow = a.rec.trace + (long long)row * a.rec.nrec +
-                                      (long long)(ry / a.rec.rsy) * a.rec.rnx;
-                        for (int e = 0; e < 4; ++e) {
-                            const int rx = gxi + e - a.rec.rx0;
-                            if (gxi + e < a.nx && rx >= 0 && rx % a.rec.rsx == 0 &&
-                                rx / a.rec.rsx < a.rec.rnx)
-                                trow[rx / a.rec.rsx] = o[e];
-                        }
-                    }
-                }
+                update_row<INJ>(a, prev, n, k, gxi, gyi, rowoff, acc, cu, pv, kv, g4, gyv * gz);
             }
 #pragma unroll
             for (int m = 0; m < 2 * R; ++m) q[m] = q[m + 1];
