@@ -362,19 +362,29 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                     xw[e][4 * m + 0] = v.x; xw[e][4 * m + 1] = v.y; xw[e][4 * m + 2] = v.z; xw[e][4 * m + 3] = v.w;
                 }
             }
-            // centre, then x pairs, per point
+            // centre, then x pairs, per point, on point pairs (0, 1) and (2, 3): for
+            // even l both operands are halves of loaded float4s, for odd l the two
+            // scalar sums land in a register pair (per lane the rounding of fmaf)
             float2 lo[2], hi[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                float acc[4];
+                const float *w = xw[e];
+                const float2 w02 = make_float2(a.w0, a.w0);
+                lo[e] = __fmul2_rn(w02, make_float2(w[R], w[R + 1]));
+                hi[e] = __fmul2_rn(w02, make_float2(w[R + 2], w[R + 3]));
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] = a.w0 * xw[e][R + i];
-#pragma unroll
-                for (int l = 1; l <= R; ++l)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) acc[i] = fmaf(a.wxy[l], xw[e][R + i + l] + xw[e][R + i - l], acc[i]);
-                lo[e] = make_float2(acc[0], acc[1]);
-                hi[e] = make_float2(acc[2], acc[3]);
+                for (int l = 1; l <= R; ++l) {
+                    float2 slo, shi;
+                    if ((l & 1) == 0) {
+                        slo = __fadd2_rn(make_float2(w[R + l], w[R + 1 + l]), make_float2(w[R - l], w[R + 1 - l]));
+                        shi = __fadd2_rn(make_float2(w[R + 2 + l], w[R + 3 + l]), make_float2(w[R + 2 - l], w[R + 3 - l]));
+                    } else {
+                        slo = make_float2(w[R + l] + w[R - l], w[R + 1 + l] + w[R + 1 - l]);
+                        shi = make_float2(w[R + 2 + l] + w[R + 2 - l], w[R + 3 + l] + w[R + 3 - l]);
+                    }
+                    lo[e] = __ffma2_rn(a.wxy2[l], slo, lo[e]);
+                    hi[e] = __ffma2_rn(a.wxy2[l], shi, hi[e]);
+                }
             }
             auto pair = [&](int e, const float2 w, const float4 &up, const float4 &dn) {
                 lo[e] = __ffma2_rn(w, __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo[e]);
