@@ -377,7 +377,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                     float2 slo, shi;
                     if ((l & 1) == 0) {
                         slo = __fadd2_rn(make_float2(w[R + l], w[R + 1 + l]), make_float2(w[R - l], w[R + 1 - l]));
-                        shi = __fadd2_rn(make_float2(w[R + 2 + l], w[R + 3 + l]), make_float2(w[R + 2 - l], w[R + 3 - l]));
+                        shi = __fadd2_rn(make_float2(w[R + 2 + l], w[R + 3 + l]),
+                                         make_float2(w[R + 2 - l], w[R + 3 - l]));
                     } else {
                         slo = make_float2(w[R + l] + w[R - l], w[R + 1 + l] + w[R + 1 - l]);
                         shi = make_float2(w[R + 2 + l] + w[R + 2 - l], w[R + 3 + l] + w[R + 3 - l]);
