@@ -132,8 +132,12 @@ def run_per_shot(shots, device=None, keep_grids=False):
 # autotuner
 # --------------------------------------------------------------------------
 
-# candidate (tx, ty, lookahead) per radius; every one is built into libfd.so
-TILES = {4: [(64, 16, 3), (64, 16, 2), (128, 8, 3), (64, 8, 3), (32, 16, 3)],
+# candidate (tx, ty, lookahead) per radius; every one is built into libfd.so.  The
+# radius-4 tiles of 160 threads (32 x 16, 64 x 8) are not offered: in a 64-shot
+# batch the 32 x 16 one gave traces differing by 1-2 ulp from the per-shot
+# kernel in a few shots, from run to run (not resolved; the 288-thread tiles
+# and the per-shot kernel were bit-identical in the same runs).
+TILES = {4: [(64, 16, 3), (64, 16, 2), (128, 8, 3)],
          8: [(32, 32, 2), (64, 8, 2), (64, 8, 3), (32, 16, 2)]}
 ZCHUNKS = [16, 32, 64, 96, 128]
 
@@ -200,7 +204,9 @@ class Autotuner:
         sizes = sorted(s.nx * s.ny * s.nz for s in shots)
         key = f"{self._gpu()}|batch|R{radii}|n{len(shots)}|p{sizes[len(sizes) // 2]}"
         if key in self.cache:
-            return {int(r): tuple(v) for r, v in self.cache[key]["launch"].items()}
+            cached = {int(r): tuple(v) for r, v in self.cache[key]["launch"].items()}
+            if all((v[0], v[1], v[3]) in TILES.get(r, []) for r, v in cached.items()):
+                return cached
         grids = [fd.grid_from_shot(s, receivers=False) for s in shots]
         choice = {}
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -50,7 +50,7 @@ def test_batch_graph_and_tiles(fdm):
     shots = small_survey(radii=(4,), count=4, seed=11)
     tr0 = batch.run_per_shot(shots)[0]
     tr1 = batch.run_batched(shots, graph_steps=4)[0]
-    tr2 = batch.run_batched(shots, graph_steps=3, launch={4: (32, 16, 20, 3)})[0]
+    tr2 = batch.run_batched(shots, graph_steps=3, launch={4: (64, 8, 20, 3)})[0]
     tr3 = batch.run_batched(shots, launch={4: (128, 8, 0, 3)})[0]
     assert batch.traces_equal(tr0, tr1) and batch.traces_equal(tr0, tr2) and batch.traces_equal(tr0, tr3)
     # both radii: the radius-8 members run on a forked stream, inside graphs too
@@ -113,6 +113,11 @@ def test_batch_errors(fdm):
     with pytest.raises(fd.FdError) as e:
         bt.set_launch(4, 48, 16, 64, 3)
     assert e.value.code == fd.FD_ERR_UNSUPPORTED
+    # built but withheld: the radius-4 32 x 16 tile (see fd_api.cpp)
+    for setter in (lambda: bt.set_launch(4, 32, 16, 64, 3), lambda: g.set_launch(32, 16, 64, 3)):
+        with pytest.raises(fd.FdError) as e:
+            setter()
+        assert e.value.code == fd.FD_ERR_UNSUPPORTED
     assert bt.run(5) == 0            # no members
     for x in (gv, g):
         x.close()
@@ -123,8 +128,8 @@ def test_autotuner_caches_a_built_choice(fdm, tmp_path):
     fd, batch = fdm
     s = small_survey(radii=(4,), count=1)[0]
     t = batch.Autotuner(path=str(tmp_path / "tune.json"))
-    c = t.single(s, steps=4, candidates=[(64, 16, 16, 3), (32, 16, 16, 3), (64, 8, 32, 3)])
-    assert c in [(64, 16, 16, 3), (32, 16, 16, 3), (64, 8, 32, 3)]
+    c = t.single(s, steps=4, candidates=[(64, 16, 16, 3), (128, 8, 16, 3), (64, 8, 32, 3)])
+    assert c in [(64, 16, 16, 3), (128, 8, 16, 3), (64, 8, 32, 3)]
     t2 = batch.Autotuner(path=str(tmp_path / "tune.json"))
     assert t2.single(s) == c                      # served from the cache
     shots = small_survey(radii=(4,), count=3)
