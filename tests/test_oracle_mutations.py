@@ -57,6 +57,24 @@ MUTATIONS = [
     ("res[(size_t)(n - 1) * (size_t)c->nrec + (size_t)r];", "res[(size_t)n * (size_t)c->nrec + (size_t)r];"),
     # caller weights: x-y weights copied into z (copy-paste slip)
     ("for (int l = 0; l <= c->r_z; ++l) cz[l] = c->cz[l];", "for (int l = 0; l <= c->r_z; ++l) cz[l] = c->cxy[l];"),
+    # VTI: delta in place of epsilon in kappa_x
+    ("double kx = v2 * (1.0 + 2.0 * eps[m]);", "double kx = v2 * (1.0 + 2.0 * delta[m]);"),
+    # VTI: source injected into q as well, whatever the setting
+    ("if (c->src_into_q) qn[idx(c, c->sx, c->sy, c->sz)] += st;", "qn[idx(c, c->sx, c->sy, c->sz)] += st;"),
+    # Ricker: factor 2 dropped from the polynomial
+    ("return (1.0 - 2.0 * a) * exp(-a);", "return (1.0 - a) * exp(-a);"),
+    # source sampled one step late
+    ("or_ricker((double)n * c->dt - c->src_t0, c->src_f);", "or_ricker((double)(n + 1) * c->dt - c->src_t0, c->src_f);"),
+    # damping: exp(-a d) instead of exp(-(a d)^2)
+    ("return exp(-ad * ad);", "return exp(-ad);"),
+    # VTI: the q equation takes Hp for Dq
+    ("qn[m] = 2.0 * qc[m] - qp[m] + kn * Hp + v2 * Dq;", "qn[m] = 2.0 * qc[m] - qp[m] + kn * Hp + v2 * Hp;"),
+    # receivers: x and y of the receiver swapped
+    ("traces[(size_t)s * (size_t)c->nrec + (size_t)r] =\n                    un[idx(c, c->rec[3 * r], c->rec[3 * r + 1],",
+     "traces[(size_t)s * (size_t)c->nrec + (size_t)r] =\n                    un[idx(c, c->rec[3 * r + 1], c->rec[3 * r],"),
+    # VTI: traces sample q instead of p
+    ("                    pn[idx(c, c->rec[3 * r], c->rec[3 * r + 1], c->rec[3 * r + 2])];",
+     "                    qn[idx(c, c->rec[3 * r], c->rec[3 * r + 1], c->rec[3 * r + 2])];"),
 ]
 
 

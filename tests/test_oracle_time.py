@@ -300,5 +300,22 @@ def test_receivers_sample_new_level(O):
         np.testing.assert_array_equal(tr[s], [u[k, j, i] for (i, j, k) in rec])
 
 
+def test_vti_receivers_sample_new_p(O):
+    """VTI traces are p^{n+1} at the receivers (p, the field the paper records;
+    with eps != delta q differs from it)."""
+    n, steps = 16, 10
+    rec = [(3, 4, 5), (8, 8, 9), (0, 15, 6)]
+    P = O.Problem(n, n, n, r_xy=4, r_z=2, h=10.0, dt=5e-4, nb=2, sponge_a=0.1, src=(8, 8, 8), receivers=rec)
+    v = np.full((n, n, n), 2000.0)
+    eps, delta = np.full_like(v, 0.2), np.full_like(v, 0.05)
+    *_, tr = P.vti_run(v, eps, delta, steps)
+    p = pp = q = qp = None
+    for s in range(steps):
+        p, pp, q, qp, _ = P.vti_run(v, eps, delta, 1, p=p, pprev=pp, q=q, qprev=qp, n0=s, traces=False)
+        np.testing.assert_array_equal(tr[s], [p[k, j, i] for (i, j, k) in rec])
+    pr, qr = np.array([p[k, j, i] for (i, j, k) in rec]), np.array([q[k, j, i] for (i, j, k) in rec])
+    assert np.all(pr != 0) and np.all(np.abs(pr - qr) > 1e-3 * np.abs(pr))
+
+
 def test_fractions_helper_consistent():
     assert _moment_solve(1) == [Fraction(-2), Fraction(1)]
