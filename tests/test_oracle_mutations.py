@@ -75,6 +75,14 @@ MUTATIONS = [
     # VTI: traces sample q instead of p
     ("                    pn[idx(c, c->rec[3 * r], c->rec[3 * r + 1], c->rec[3 * r + 2])];",
      "                    qn[idx(c, c->rec[3 * r], c->rec[3 * r + 1], c->rec[3 * r + 2])];"),
+    # VTI damping: the older level of q left undamped
+    ("pn[m] *= g; pc[m] *= g; qn[m] *= g; qc[m] *= g;", "pn[m] *= g; pc[m] *= g; qn[m] *= g;"),
+    # x-y stencil: one y neighbour counted twice (copy-paste slip)
+    ("at(u, c, i, j + l, k) + at(u, c, i, j - l, k));", "at(u, c, i, j + l, k) + at(u, c, i, j + l, k));"),
+    # VTI: Dq taken of p
+    ("double Dq = op_z(c, cz, qc, i, j, k);\n", "double Dq = op_z(c, cz, pc, i, j, k);\n"),
+    # VTI: Hp taken of q
+    ("double Hp = op_h(c, cw, pc, i, j, k);\n", "double Hp = op_h(c, cw, qc, i, j, k);\n"),
 ]
 
 
