@@ -243,7 +243,9 @@ int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead);
  * one second) runs out; the CTA records the timeout in the grid's status
  * block, waits (bounded) for its copies in flight and exits, and the next
  * fd_sync / host read-back returns FD_ERR_TIMEOUT.  The context stays usable;
- * the grid's results are then undefined and its status stays failed.  Not for
+ * the grid's results are then undefined and its status stays failed.  With
+ * g == NULL the hook applies to the next fd_iso_step_static() call made on the
+ * calling host thread (plane checked against that call's grid).  Not for
  * production use.
  */
 int fd_debug_skip_copy(fd_grid_t *g, int plane);
@@ -370,26 +372,34 @@ int fd_batch_destroy(fd_batch_t *b);
  * latency-critical loop that cannot take the device-wide synchronisation that
  * cudaMalloc / cudaFree may cause -- and so cannot use fd_create_grid().
  *
- * Same arithmetic and kernel as fd_step() on an isotropic grid: u_prev holds
- * the stored older level on entry and u^{n+1} on return (in place), u_cur is
- * u^n, kappa = (v dt)^2; all three are device arrays in the pitched layout of
- * fd_layout(d) (16-byte aligned), owned by the caller.  n is the time index of
- * u_cur and selects the Ricker sample s(n dt - t0) of the source at (src_ix,
- * src_iy, src_iz); src_ix < 0 means no source.  No receivers.  Asynchronous
- * on `stream`.
+ * Same arithmetic and kernel as fd_step() on an isotropic grid, and the same
+ * results bit for bit: u_prev holds the stored older level on entry and
+ * u^{n+1} on return (in place), u_cur is u^n, kappa = (v dt)^2; all three are
+ * device arrays in the pitched layout of fd_layout(d) (16-byte aligned), owned
+ * by the caller.  n is the time index of u_cur and selects the Ricker sample
+ * s(n dt - t0) of the source at (src_ix, src_iy, src_iz); src_ix < 0 means no
+ * source.  No receivers.  status (optional, device memory owned by the caller,
+ * NULL to skip) receives FD_OK, or FD_ERR_TIMEOUT when a bounded device wait
+ * of the sweep ran out (the step's output is then undefined); it is written
+ * on `stream` after the sweep.  Asynchronous on `stream`: the call enqueues
+ * kernels only and makes the host wait for nothing.
  *
  * Its scratch (status block, damping profiles, source sample) lives in a
  * fixed __device__ array of about 97 KiB that every GPU loading the library
- * holds until exit.  Grids with an axis above FD_STATIC_MAX_AXIS points are
- * rejected with FD_ERR_OUT_OF_RANGE.  Every call rewrites that array on its
- * stream, so calls that may overlap on the GPU (different streams or host
- * threads without ordering) race; the first call on a device looks up the
- * array's address and should come before any stream capture on that device.
+ * holds until exit.  Grids with an axis above FD_STATIC_MAX_AXIS points, or a
+ * damping layer wider than FD_STATIC_MAX_SPONGE cells, are rejected with
+ * FD_ERR_OUT_OF_RANGE.  Every call rewrites that array on its stream, so
+ * calls that may overlap on the GPU (different streams or host threads
+ * without ordering) race; the first call on a device looks up the array's
+ * address and should come before any stream capture on that device.
+ * fd_debug_skip_copy(NULL, plane) arms the failure-detection hook for the next
+ * call made on the same host thread.
  */
 #define FD_STATIC_MAX_AXIS 8192
+#define FD_STATIC_MAX_SPONGE 512
 int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u_prev, const float *kappa,
                        int n, int src_ix, int src_iy, int src_iz, double freq_hz, double t0,
-                       double amp, void *stream);
+                       double amp, int *status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -1004,7 +1004,12 @@ int fd_halo_exchange(fd_grid_t *lo, fd_grid_t *up, int planes)
 
 int fd_debug_skip_copy(fd_grid_t *g, int plane)
 {
-    if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
+    if (!g) {
+        // the next fd_iso_step_static() on this host thread
+        if (plane < 0) return fail(FD_ERR_INVALID_ARG, "plane %d is negative", plane);
+        t_static_skip = plane;
+        return FD_OK;
+    }
     if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "the hook is in the isotropic sweep");
     if (plane < 0 || plane >= g->d.nz) return fail(FD_ERR_INVALID_ARG, "plane %d outside 0..%d", plane, g->d.nz - 1);
     g->debug_skip = plane;

@@ -84,6 +84,10 @@ struct VtiArgs {
     unsigned int ncta;
 };
 
+// fd_debug_skip_copy(NULL, plane) arms the hook for the next fd_iso_step_static()
+// call on the calling host thread (-1 = none).
+extern thread_local int t_static_skip;
+
 // Launch configuration of one sweep.
 struct Launch {
     int tx, ty;             // tile (x multiple of 4)

@@ -106,7 +106,7 @@ def lib() -> ctypes.CDLL:
             "fd_sync": [_vp],
             "fd_destroy_grid": [_vp],
             "fd_last_error": [ctypes.c_char_p, ctypes.c_size_t],
-            "fd_iso_step_static": [D, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _d, _vp],
+            "fd_iso_step_static": [D, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _d, _vp, _vp],
             "fd_batch_create": [_vp, ctypes.POINTER(_vp)],
             "fd_batch_set_launch": [_vp, _i, _i, _i, _i, _i],
             "fd_batch_set_graph": [_vp, _i],
@@ -265,12 +265,13 @@ def fd_destroy_grid(g) -> None:
 
 
 def fd_iso_step_static(d: fd_desc, u_cur, u_prev, kappa, n, src=None, freq_hz=15.0, t0=None,
-                       amp=1.0, stream=0) -> None:
-    """One isotropic step with no device allocation (see include/fd.h)."""
+                       amp=1.0, status=None, stream=0) -> None:
+    """One isotropic step with no device allocation (see include/fd.h).
+    `status`: optional device int32 tensor that receives FD_OK or FD_ERR_TIMEOUT."""
     sx, sy, sz = (-1, -1, -1) if src is None else src
     t0 = 1.0 / freq_hz if t0 is None else t0
     _check(lib().fd_iso_step_static(ctypes.byref(d), _ptr(u_cur), _ptr(u_prev), _ptr(kappa), n,
-                                    sx, sy, sz, freq_hz, t0, amp, stream))
+                                    sx, sy, sz, freq_hz, t0, amp, _ptr(status), stream))
 
 
 def fd_set_injection(g, idx, nrec, values_dev, nt_cap) -> None:
