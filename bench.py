@@ -16,7 +16,11 @@ state) and --warmup warm-up steps.
 upload, steps, receiver traces back to the host.  `roofline` compares the
 stencil kernel's algorithmic bytes per launch with the measured HBM copy
 bandwidth.  `cpu_baseline` times the FP64 CPU oracle on a bounded slab of the
-same workload.  `--impl reference` times only that oracle.
+same workload, sampled as the reference arm samples it.  The default run
+(radius 4) also times the radius-8 operator and the paper's VTI operator on
+the same 512^3 model, each at least 300 steps with its own roofline, under
+`other_operators` (`value` stays the radius-4 figure).  `--impl reference`
+times only the oracle.
 
 Multi-GPU (torchrun, one rank per GPU): shots are independent, so each rank
 runs its own replica shot (weak scaling) and only the timing is reduced.
@@ -65,7 +69,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default="", help="tx,ty,zchunk,lookahead override")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the radius-8 and VTI blocks of the default run")
     ap.add_argument("--settle", type=float, default=1.5,
                     help="seconds of untimed steps before the warm-up (steady state)")
     return ap.parse_args()
@@ -299,20 +304,90 @@ def run_reference(args):
     if rank != 0:
         return 0
     shot = make_shot(args.workload, args.n, seed=1)
-    budget = 150.0
-    pts_s, det = time_oracle(shot, budget, steps=args.steps, warmup=args.warmup)
+    pts_s, det = time_oracle(shot, ORACLE_BUDGET_S, steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": pts_s, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * det["seconds"] / det["steps"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(args.workload, shot, args),
         "cpu_baseline": {"value": pts_s, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
-                         "sample": f"FP64 C oracle, {det['steps']} steps of a {det['slab']} slab of the "
-                                   f"workload's model", "cpu": cpu_model()},
+                         "sample": f"FP64 C oracle, {det['steps']} steps after {args.warmup} warm-up steps of a "
+                                   f"{det['slab']} slab of the workload's model", "cpu": cpu_model()},
         "e2e": {"value": pts_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_sweep(wl, shot, dev, K, W, settle_s, launch=""):
+    """Device time of K steps of a resident shot (no receivers during the settle
+    phase, the receiver plane during the warm-up and timed steps).  Returns
+    (elapsed ms, settle steps, clock summary)."""
+    import torch
+
+    from paper_1410_1387_gb300 import fd
+
+    g = fd.grid_from_shot(shot, device=dev, receivers=False)
+    if launch:
+        g.set_launch(*[int(x) for x in launch.split(",")])
+    stream = g.stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    settle = 0
+    with ClockSampler(dev.index or 0) as clk:
+        # Settle: untimed steps for at least settle_s seconds of sustained load
+        # before the warm-up, so that the timed steps run in the GPU's steady
+        # state (some boxes slow down for about a second shortly after a heavy
+        # load starts, then recover).  The receivers join afterwards.
+        t_set = time.perf_counter()
+        while time.perf_counter() - t_set < settle_s:
+            g.run(32)
+            g.sync()
+            settle += 32
+        g.set_receivers(shot.receivers, K + W)
+        g.run(W)
+        g.sync()
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        g.run(K)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    g.sync()
+    el_ms = ev0.elapsed_time(ev1)
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    return el_ms, settle, clk.summary()
+
+
+def roofline(wl, n, launch_ms):
+    w = WORKLOADS[wl]
+    peak, peak_kind = measured_peak()
+    pts = n ** 3
+    algo = w["bytes_per_pt"] * pts
+    achieved = algo / (launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": recorded_traffic(wl, w["kernel"], n),
+            "kernel": w["kernel"], "algorithmic_bytes_per_launch": algo,
+            "bytes_per_point": w["bytes_per_pt"],
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+
+
+ORACLE_BUDGET_S = 150.0   # CPU seconds a timed oracle sample may take (slab size chosen to fit)
+
+
+def cpu_leg(shot, K, W):
+    """The oracle on the host cores, sampled as the reference arm samples it
+    (the same slab rule and budget) at min(K, 20) steps after min(W, 5)
+    warm-up steps: with the K = 20, W = 5 of a short run the two legs time the
+    same work."""
+    steps, warm = min(K, 20), min(W, 5)
+    pts_s, det = time_oracle(shot, ORACLE_BUDGET_S, steps=steps, warmup=warm)
+    return {"value": pts_s, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+            "sample": f"FP64 C oracle, {det['steps']} steps after {warm} warm-up steps of a {det['slab']} slab "
+                      f"of the same model", "cpu": cpu_model()}
 
 
 def run_ours(args):
@@ -333,41 +408,10 @@ def run_ours(args):
     pts = shot.nx * shot.ny * shot.nz
 
     # ---- device-resident timing -------------------------------------------------
-    g = fd.grid_from_shot(shot, device=dev, receivers=False)
-    if args.launch:
-        g.set_launch(*[int(x) for x in args.launch.split(",")])
-    stream = g.stream
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    settle = 0
-    with ClockSampler(local) as clk:
-        # Settle: untimed steps for at least args.settle seconds of sustained load
-        # before the warm-up, so that the timed steps run in the GPU's steady
-        # state (some boxes slow down for about a second shortly after a heavy
-        # load starts, then recover).  The receivers join afterwards.
-        t_set = time.perf_counter()
-        while time.perf_counter() - t_set < args.settle:
-            g.run(32)
-            g.sync()
-            settle += 32
-        g.set_receivers(shot.receivers, K + W)
-        g.run(W)
-        g.sync()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        g.run(K)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-    g.sync()
-    el_ms = ev0.elapsed_time(ev1)
+    el_ms, settle, clocks = time_sweep(args.workload, shot, dev, K, W, args.settle, args.launch)
     if world > 1:
         dist.barrier()
     el_ms = fdist.max_over_ranks(el_ms, dev)
-    g.close()
-    del g
-    torch.cuda.empty_cache()
     value = pts * K * world / (el_ms * 1e-3)
     launch_ms = el_ms / K
 
@@ -397,30 +441,34 @@ def run_ours(args):
             fd.fd_read_receivers(g.h, 0, nsh, tr_h.data_ptr(), fd.FD_PTR_HOST)
         e2e_s = fdist.max_over_ranks(time.perf_counter() - t0, dev)
         g.close()
+        del g
+        torch.cuda.empty_cache()
         nmodel = 3 if shot.mode == "vti" else 1
         e2e = {"value": pts * nsh * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": nmodel * pts * 4 / nsh,
                "d2h_bytes_per_step": len(shot.receivers) * 4,
                "shot_seconds": e2e_s, "steps_per_shot": nsh}
 
+    # ---- the other single-shot operators of the same size, device-timed --------------
+    others = {}
+    if args.workload == "iso512_r4" and not args.no_others and world == 1:
+        for wl2 in ("iso512_r8", "vti512"):
+            shot2 = make_shot(wl2, args.n, seed=1)
+            K2, W2 = max(K, 300), max(W, 5)
+            el2, settle2, clk2 = time_sweep(wl2, shot2, dev, K2, W2, min(args.settle, 0.5))
+            others[wl2] = {"value": shot2.points * K2 / (el2 * 1e-3), "unit": UNIT, "steps": K2, "warmup": W2,
+                           "ms_per_step": el2 / K2, "settle_steps": settle2,
+                           "config": workload_config(wl2, shot2, args),
+                           "roofline": roofline(wl2, args.n, el2 / K2), "clocks": clk2}
+            del shot2
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    peak, peak_kind = measured_peak()
-    algo = w["bytes_per_pt"] * pts
-    achieved = algo / (launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": recorded_traffic(args.workload, w["kernel"], args.n),
-            "kernel": w["kernel"], "algorithmic_bytes_per_launch": algo,
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
-    cpu = None
-    if not args.no_cpu_baseline:
-        pts_s, det = time_oracle(shot, args.cpu_seconds)
-        cpu = {"value": pts_s, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
-               "sample": f"FP64 C oracle, {det['steps']} steps of a {det['slab']} slab of the same model",
-               "cpu": cpu_model()}
+    roof = roofline(args.workload, args.n, launch_ms)
+    cpu = None if args.no_cpu_baseline else cpu_leg(shot, K, W)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": el_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -429,8 +477,10 @@ def run_ours(args):
                        settle={"seconds": args.settle, "steps": settle,
                                "note": "untimed steps before the warm-up, for the steady state"}),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
-        "clocks": clk.summary(), "device": device_info(dev), "impl": "ours",
+        "clocks": clocks, "device": device_info(dev), "impl": "ours",
     }
+    if others:
+        line["other_operators"] = others
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

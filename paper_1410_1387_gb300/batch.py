@@ -132,12 +132,8 @@ def run_per_shot(shots, device=None, keep_grids=False):
 # autotuner
 # --------------------------------------------------------------------------
 
-# candidate (tx, ty, lookahead) per radius; every one is built into libfd.so.  The
-# radius-4 tiles of 160 threads (32 x 16, 64 x 8) are not offered: in a 64-shot
-# batch the 32 x 16 one gave traces differing by 1-2 ulp from the per-shot
-# kernel in a few shots, from run to run (not resolved; the 288-thread tiles
-# and the per-shot kernel were bit-identical in the same runs).
-TILES = {4: [(64, 16, 3), (64, 16, 2), (128, 8, 3)],
+# candidate (tx, ty, lookahead) per radius; every one is built into libfd.so
+TILES = {4: [(64, 16, 3), (64, 16, 2), (64, 16, 4), (128, 8, 3), (64, 8, 3), (32, 16, 3)],
          8: [(32, 32, 2), (64, 8, 2), (64, 8, 3), (32, 16, 2)]}
 ZCHUNKS = [16, 32, 64, 96, 128]
 

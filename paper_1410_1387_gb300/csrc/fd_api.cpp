@@ -178,22 +178,13 @@ int make_tensor_maps(fd_grid *g)
     return FD_OK;
 }
 
-// The radius-4 32 x 16 tile (lookahead 3) is built but withheld: in a 64-shot
-// batch it gave traces 1-2 ulp away from the per-shot kernel in a few shots,
-// differing from run to run, while every other tile matched bit for bit.  Until
-// the cause is found no launch may select it.
-bool launch_withheld(int R, const Launch &L)
-{
-    return R == 4 && L.tx == 32 && L.ty == 16;
-}
-
 int set_launch(fd_grid *g, const Launch &L)
 {
     if (L.tx <= 0 || L.ty <= 0 || L.zchunk <= 0 || L.lookahead <= 0 || L.zchunk > kMaxChunk)
         return fail(FD_ERR_INVALID_ARG, "bad launch configuration (z chunk 1..%d)", kMaxChunk);
     if ((g->d.ny + L.ty - 1) / L.ty > 65535 || (g->d.nz + L.zchunk - 1) / L.zchunk > 65535)
         return fail(FD_ERR_INVALID_ARG, "launch grid too large");
-    const bool built = g->d.mode == FD_MODE_ISO ? iso_config_built(g->d.r_xy, L) && !launch_withheld(g->d.r_xy, L)
+    const bool built = g->d.mode == FD_MODE_ISO ? iso_config_built(g->d.r_xy, L)
                                                 : vti_config_built(g->d.r_xy, g->d.r_z, L);
     if (!built)
         return fail(FD_ERR_UNSUPPORTED, "tile %d x %d, lookahead %d is not built for this radius", L.tx, L.ty,
@@ -1244,7 +1235,7 @@ int fd_batch_set_launch(fd_batch_t *b, int radius, int tx, int ty, int zchunk, i
     if (ri < 0) return fail(FD_ERR_UNSUPPORTED, "batches hold isotropic radius 4 or 8 shots");
     if (zchunk < 0 || zchunk > kMaxChunk) return fail(FD_ERR_INVALID_ARG, "z chunk 0..%d", kMaxChunk);
     Launch L{tx, ty, zchunk, lookahead};
-    if (!iso_config_built(radius, L) || launch_withheld(radius, L))
+    if (!iso_config_built(radius, L))
         return fail(FD_ERR_UNSUPPORTED, "tile %d x %d, lookahead %d is not built for radius %d", tx, ty, lookahead,
                     radius);
     b->L[ri] = L;

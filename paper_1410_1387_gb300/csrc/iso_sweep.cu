@@ -83,22 +83,23 @@ struct IsoCfg {
 // of the shot's ncta CTAs advances it (so graph replays need no per-step
 // arguments).  Returns -1 to every thread when n >= n_end (a finished shot in a
 // batch: its CTAs do nothing).
+// step_take is the part of one thread; step_prologue shares its result with the CTA.
+__device__ __forceinline__ int step_take(DevState *st, unsigned ncta, int n_end)
+{
+    int n = *reinterpret_cast<volatile int *>(&st->step);
+    if (n >= n_end) return -1;
+    __threadfence();
+    if (atomicAdd(&st->done, 1u) == ncta - 1) {
+        st->done = 0;
+        *reinterpret_cast<volatile int *>(&st->step) = n + 1;
+        __threadfence();
+    }
+    return n;
+}
+
 __device__ __forceinline__ int step_prologue(DevState *st, unsigned ncta, int n_end, int *sh_n)
 {
-    if (threadIdx.x == 0) {
-        int n = *reinterpret_cast<volatile int *>(&st->step);
-        if (n >= n_end) {
-            n = -1;
-        } else {
-            __threadfence();
-            if (atomicAdd(&st->done, 1u) == ncta - 1) {
-                st->done = 0;
-                *reinterpret_cast<volatile int *>(&st->step) = n + 1;
-                __threadfence();
-            }
-        }
-        *sh_n = n;
-    }
+    if (threadIdx.x == 0) *sh_n = step_take(st, ncta, n_end);
     __syncthreads();
     return *sh_n;
 }
@@ -171,10 +172,13 @@ __device__ __forceinline__ void update_row(const IsoArgs &a, float *prev, const 
 // the adjoint's velocity-gradient term: `cur` is the forward level a = u^n,
 // ring B carries z (tm_prev), kappa and the gradient (tm_grad), and each point
 // gets grad += a.c2dt z (L a) / sqrt(kappa), written over the gradient (`prev`).
-template <int R, int TX, int TY, int LA, bool INJ, bool GRAD = false>
+// DEP: the launch is a programmatic dependent of the previous step's: the CTA
+// sets up its barriers (and tensor memory) before it waits for that step to
+// complete, then takes its time index itself (`n` is ignored).
+template <int R, int TX, int TY, int LA, bool INJ, bool GRAD = false, bool DEP = false>
 __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtensorMap *tm_prev,
                                          const CUtensorMap *tm_kappa, const CUtensorMap *tm_ctile, const IsoArgs &a,
-                                         float *prev, const float *cur, const int n, const int bx, const int by,
+                                         float *prev, const float *cur, int n, const int bx, const int by,
                                          const int bz, const CUtensorMap *tm_grad = nullptr)
 {
     using C = IsoCfg<R, TX, TY, LA, GRAD ? 3 : 2>;
@@ -211,24 +215,34 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         sh[2] = z0;
         sh[3] = z0;
     }
-    float *sgz = reinterpret_cast<float *>(smem_raw + C::OFF_GZ);   // z damping factors of the chunk
-    for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
+    if (tid == C::NC) {
+        prefetch_tmap(tm_cur);
+        prefetch_tmap(tm_prev);
+        prefetch_tmap(tm_kappa);
+        prefetch_tmap(tm_ctile);
+    }
     if constexpr (TQ) {
         __syncwarp();
         if (tid < 32) tmem_alloc(sh_tmem, C::TMEM_COLS);
-        tmem_fence_before_sync();
     }
+    if constexpr (DEP) {
+        // Nothing above reads what the previous step writes.  From here on the
+        // time index, u^n and the tables (a preceding kernel may have written
+        // them) must be that step's.
+        griddep_wait();
+        if (tid == 0) sh[0] = step_take(a.st, a.ncta, 0x7fffffff);
+    }
+    float *sgz = reinterpret_cast<float *>(smem_raw + C::OFF_GZ);   // z damping factors of the chunk
+    for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
+    if constexpr (TQ) tmem_fence_before_sync();
     __syncthreads();
     if constexpr (TQ) tmem_fence_after_sync();
+    if constexpr (DEP) n = sh[0];
     bool failed = false;
 
     if (tid >= C::NC) {
         // ------------------------------------------------------------ producer warp
         if (tid == C::NC) {
-            prefetch_tmap(tm_cur);
-            prefetch_tmap(tm_prev);
-            prefetch_tmap(tm_kappa);
-            prefetch_tmap(tm_ctile);
             int a_end = z0, b_end = z0;             // planes issued: A [z0, a_end), B [z0, b_end)
             bool ok = true;
             // test hook (fd_debug_skip_copy): CTA (0,0,0) withholds one plane's copy,
@@ -404,7 +418,9 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 up0 = up1;
                 dn1 = dn0;
             }
-            // this warp no longer reads plane k from either ring
+            // this warp no longer reads plane k from either ring: order its plain
+            // reads before the producer's next copies into these slots
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&emptyA[sa]);
@@ -535,7 +551,9 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 lo = __ffma2_rn(a.wxy2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo);
                 hi = __ffma2_rn(a.wxy2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi);
             }
-            // this warp no longer reads plane k from either ring
+            // this warp no longer reads plane k from either ring: order its plain
+            // reads before the producer's next copies into these slots
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&emptyA[sa]);
@@ -609,11 +627,10 @@ __global__ void __launch_bounds__(IsoCfg<R, TX, TY, LA>::NT, IsoCfg<R, TX, TY, L
                      const __grid_constant__ CUtensorMap tm_kappa, const __grid_constant__ CUtensorMap tm_ctile,
                      const __grid_constant__ IsoArgs a)
 {
-    using C = IsoCfg<R, TX, TY, LA>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int n = step_prologue(a.st, a.ncta, 0x7fffffff, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
-    iso_body<R, TX, TY, LA, INJ>(&tm_cur, &tm_prev, &tm_kappa, &tm_ctile, a, a.prev, a.cur, n, blockIdx.x, blockIdx.y,
-                                 blockIdx.z);
+    // the next step's CTAs may start their set-up while this step's last ones run
+    griddep_launch_dependents();
+    iso_body<R, TX, TY, LA, INJ, false, true>(&tm_cur, &tm_prev, &tm_kappa, &tm_ctile, a, a.prev, a.cur, 0, blockIdx.x,
+                                              blockIdx.y, blockIdx.z);
 }
 
 // Batched step: one launch advances every member shot of a batch by one step.
@@ -638,6 +655,14 @@ __global__ void __launch_bounds__(IsoCfg<R, TX, TY, LA>::NT, IsoCfg<R, TX, TY, L
     const int n = step_prologue(b.a.st, b.ncta, b.n_end, reinterpret_cast<int *>(smem_raw + C::OFF_GZ - 16));
     if (n < 0) return;
     const int c = b.cur0 ^ ((n - b.n0) & 1);      // buffer holding u^n
+    if (threadIdx.x == C::NC) {
+        // the maps sit in the batch's descriptor table, rewritten by host copies
+        // whenever the membership changes: the issuing thread acquires them
+        fence_tmap_acquire(&b.halo[c]);
+        fence_tmap_acquire(&b.tile[0]);
+        fence_tmap_acquire(&b.tile[1]);
+        fence_tmap_acquire(&b.kappa);
+    }
     iso_body<R, TX, TY, LA, false>(&b.halo[c], &b.tile[c ^ 1], &b.kappa, &b.tile[c], *sa, b.buf[c ^ 1], b.buf[c], n, it.y,
                                    it.z, it.w);
 }
@@ -664,8 +689,23 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
     const int smem = cmax(C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4), C::SMEM_FLOOR);
-    iso_sweep_kernel<R, TX, TY, LA, INJ><<<grid, C::NT, smem, s>>>(tm.cur, tm.prev, tm.kappa, tm.cur_tile, a);
-    return cudaGetLastError();
+    // Programmatic stream serialisation: consecutive steps overlap one CTA's
+    // set-up with the previous step's last CTAs (each CTA waits for that step
+    // to complete before it reads anything the step writes).  Measured at
+    // 512^3: +0.7 % for the register-queue forms, -2.8 % for the radius-8
+    // tensor-memory form, which is therefore launched without it (its
+    // griddepcontrol instructions then return at once).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = C::TQ ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, iso_sweep_kernel<R, TX, TY, LA, INJ>, tm.cur, tm.prev, tm.kappa, tm.cur_tile, a);
 }
 
 template <int R, int TX, int TY, int LA>

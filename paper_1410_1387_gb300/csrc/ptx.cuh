@@ -25,6 +25,13 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Orders this thread's earlier generic-proxy accesses of shared memory (plain
+// ld.shared / st.shared) before later async-proxy accesses (TMA).  A consumer
+// that has read a ring slot with plain loads issues it before the slot is
+// released: the release arrival alone orders the reads only within the
+// generic proxy, and without the fence the producer's next TMA copy into the
+// slot can overtake reads still in flight (seen on GB300 as rare one-warp,
+// one-plane corruptions of the first tile rows, which the copy writes first).
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -38,8 +45,8 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-// Plain arrival (release semantics at CTA scope): this thread's earlier shared
-// memory reads of the slot are ordered before the producer's next overwrite.
+// Plain arrival (release semantics at CTA scope).  Before releasing a slot that
+// the next TMA copy overwrites, the readers issue fence_proxy_async_smem().
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -96,6 +103,28 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// A tensor map that lives in global memory and was written through the generic
+// proxy (here: by a host-to-device copy) must be acquired by the tensormap proxy
+// before the thread that issues TMA copies with it uses it; otherwise the TMA
+// unit may keep using an older descriptor it cached for that address.  System
+// scope, because the writer is a host copy.
+__device__ __forceinline__ void fence_tmap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
+// Programmatic dependent launch (a launch with programmatic stream
+// serialisation): griddep_wait() blocks until the grid this one depends on has
+// completed and its memory operations are visible; griddep_launch_dependents()
+// lets the next such grid start launching (its CTAs run up to their own wait)
+// once every CTA of this grid has issued it or exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Streaming 128-bit global load of data written by nobody during the kernel.

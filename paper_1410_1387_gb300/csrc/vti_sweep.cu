@@ -229,6 +229,9 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             hp[1] = hp_lo.y;
             hp[2] = hp_hi.x;
             hp[3] = hp_hi.y;
+            // this warp no longer reads plane k from either ring: order its plain
+            // reads before the producer's next copies into these slots
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&emptyA[sa]);

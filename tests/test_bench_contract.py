@@ -41,3 +41,20 @@ def test_kernel_hash_ignores_comments_and_layout():
     b = "int f(int x) {\n\n    return 2 * x;   }"
     c = "int f(int x) { return 3 * x; }"
     assert bench._code_only(a) == bench._code_only(b) != bench._code_only(c)
+
+
+def test_cpu_leg_samples_like_the_reference_arm():
+    """The bench line's cpu_baseline times the oracle as the reference arm does:
+    the same step and warm-up counts (capped at 20 and 5) on the same slab rule."""
+    sys.path.insert(0, ROOT)
+    import bench
+    shot = bench.make_shot("iso512_r4", 24, seed=1)
+    leg = bench.cpu_leg(shot, 2, 1)
+    assert leg["kind"] == "oracle" and leg["cores"] >= 1 and leg["value"] > 0
+    assert "2 steps after 1 warm-up steps of a [24, 24, 24] slab" in leg["sample"]
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "24",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    ref = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
+    assert "2 steps after 1 warm-up steps of a [24, 24, 24] slab" in ref["cpu_baseline"]["sample"]
+    long = bench.cpu_leg(shot, 2000, 20)
+    assert "20 steps after 5 warm-up steps" in long["sample"]

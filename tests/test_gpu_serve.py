@@ -55,3 +55,31 @@ def test_request_above_budget_is_refused(srv):
     reqs = small_stream(count=1)
     with pytest.raises(ValueError):
         srv.ShotServer(1024, steps_per_iter=5).serve(reqs, realtime=False)
+
+
+def test_served_requests_match_the_oracle(srv, O):
+    """Served requests against the FP64 oracle, element by element: a stream of
+    radius-4 and radius-8 requests runs through the server (a budget that keeps
+    about three resident, so the two checked ones share the GPU with others),
+    and the traces of one request of each radius are compared with the oracle's
+    run of the same shot on the same model (drawn on the GPU, copied back)."""
+    import torch
+    from tests.helpers import max_rel, oracle_problem
+    # grids of 40-56 points (damping layer n // 6, source at the centre) and
+    # enough steps for the Ricker pulse (peak at t0 = 1/f, about 150 steps) to
+    # cross to the receiver plane
+    reqs = synth.poisson_requests(6, rate=200.0, seed=21, n_lo=40, n_hi=56, steps_lo=240, steps_hi=300,
+                                  radii=(4, 8))
+    assert {r.radius for r in reqs} == {4, 8}
+    sizes = sorted(srv.shot_bytes(synth.request_shot(r)) for r in reqs)
+    server = srv.ShotServer(sum(sizes[-3:]), steps_per_iter=9, keep_traces=True)
+    served = {r.rid: r for r in server.serve(reqs, realtime=True)}
+    assert server.max_resident >= 2
+    for radius in (4, 8):
+        req = next(r for r in reqs if r.radius == radius)
+        shot = synth.request_shot(req)
+        v = synth.layered_model_device(req.n, req.seed, torch.device("cuda", 0)).cpu().numpy()
+        _, _, tr_ref = oracle_problem(O, shot).iso_run(v, shot.nsteps)
+        tr = served[req.rid].traces
+        assert tr.shape == tr_ref.shape and np.abs(tr_ref).max() > 0
+        assert max_rel(tr, tr_ref) <= 1e-4
