@@ -291,6 +291,18 @@ int fd_set_z_window(fd_grid_t *g, int kg0, int nz_global);
    between ranks instead. */
 int fd_halo_exchange(fd_grid_t *lower, fd_grid_t *upper, int planes);
 
+/* Part of one time step (Eq. 3 at planes [k_begin, k_end) only; every point
+   still reads u^n within R of it, ghost planes included).  A step may be
+   enqueued as several parts on g's stream, each plane in at most one part;
+   the part with complete != 0 comes last: it advances the time index, samples
+   gathered receivers and makes the new level current.  Planes no part covers
+   keep their older stored value -- a slab's ghost planes, which the exchange
+   then overwrites.  This lets a slab update the planes its neighbours need
+   first, start their exchange, and update its interior while the planes are
+   in flight.  Parts run outside any CUDA graph.  FD_ERR_INVALID_ARG for an
+   empty or out-of-range range; otherwise as fd_step. */
+int fd_step_planes(fd_grid_t *g, int k_begin, int k_end, int complete);
+
 /* ---- adjoint and velocity gradient -----------------------------------------
  * For J = 1/2 sum_n sum_r (u^{n+1}(x_r) - dobs[n][r])^2 of an isotropic run
  * (an extension: the paper computes no gradients; its use is imaging).  The

@@ -221,7 +221,9 @@ IsoArgs iso_args(const fd_grid *g)
     return a;
 }
 
-cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
+// Planes [zb, nz - ztop) of the step from level `cur`; hold = 1: a later part
+// completes the step (advances the time index and samples gathered receivers).
+cudaError_t enqueue_part(fd_grid *g, int cur, int zb, int ztop, int hold, cudaStream_t s)
 {
     const fd_desc &d = g->d;
     Source src{g->src_tab, g->src_len, g->sx, g->sy, g->sz, g->into_q};
@@ -236,6 +238,9 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
         a.cur = g->field[cur];
         a.skip_plane1 = g->debug_skip + 1;
         g->debug_skip = -1;
+        a.zb = zb;
+        a.ztop = ztop;
+        a.hold = hold;
         const IsoMaps maps{g->tm_halo[cur], g->tm_tile[1 - cur], g->tm_model[0], g->tm_tile[cur]};
         e = launch_iso(d.r_xy, g->L, maps, a, s);
         newbuf = a.prev;
@@ -255,17 +260,20 @@ cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s)
         std::memcpy(a.wxy, g->wxy, sizeof a.wxy);
         for (int l = 0; l <= kMaxR; ++l) a.wxy2[l] = make_float2(g->wxy[l], g->wxy[l]);
         a.src = src; a.rec = rec; a.st = g->st;
+        a.zb = zb; a.ztop = ztop; a.hold = hold;
         const VtiMaps maps{g->tm_halo[cur],    g->tm_tile[2 + cur], g->tm_tile[1 - cur], g->tm_tile[3 - cur],
                            g->tm_model[0],     g->tm_model[1],      g->tm_model[2]};
         e = launch_vti(d.r_xy, d.r_z, g->L, maps, a, s);
         newbuf = a.pprev;
     }
     if (e != cudaSuccess) return e;
-    if (g->nrec > 0 && !g->lattice)
+    if (!hold && g->nrec > 0 && !g->lattice)
         e = launch_gather(newbuf, pitch, plane, g->rec_idx, g->nrec, g->trace, g->rec_t0, g->rec_cap,
                           g->st, s);
     return e;
 }
+
+cudaError_t enqueue_step(fd_grid *g, int cur, cudaStream_t s) { return enqueue_part(g, cur, 0, 0, 0, s); }
 
 int check_ready(fd_grid *g, int nsteps)
 {
@@ -783,6 +791,21 @@ int fd_set_graph(fd_grid_t *g, int steps)
         return fail(FD_ERR_INVALID_ARG, "graph steps must be 0 or even in 2..1024");
     drop_graphs(g);
     g->graph_steps = steps;
+    return FD_OK;
+}
+
+int fd_step_planes(fd_grid_t *g, int k_begin, int k_end, int complete)
+{
+    int rc = check_ready(g, 1);
+    if (rc) return rc;
+    if (k_begin < 0 || k_end > g->d.nz || k_begin >= k_end)
+        return fail(FD_ERR_INVALID_ARG, "planes [%d, %d) are not a non-empty range of 0..%d", k_begin, k_end, g->d.nz);
+    cudaError_t e = enqueue_part(g, g->cur, k_begin, g->d.nz - k_end, complete ? 0 : 1, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    if (complete) {
+        g->cur ^= 1;
+        g->n += 1;
+    }
     return FD_OK;
 }
 

@@ -63,6 +63,9 @@ struct alignas(16) IsoArgs {
     unsigned int ncta;
     float c2dt;             // 2 dt: the gradient sweep's factor
     int skip_plane1;        // test hook: 1 + a plane whose u^n copy CTA (0,0,0) withholds (0 = none)
+    // Part of a step (all zero: the whole step): planes [zb, nz - ztop) are
+    // updated; hold = 1 leaves the time index for a later part to advance.
+    int zb, ztop, hold;
 };
 
 // Arguments of the VTI sweep (Eqs. 1-2, 4-5).
@@ -82,6 +85,7 @@ struct VtiArgs {
     RecLattice rec;
     DevState *st;
     unsigned int ncta;
+    int zb, ztop, hold;     // part of a step, as in IsoArgs (all zero: the whole step)
 };
 
 // fd_debug_skip_copy(NULL, plane) arms the hook for the next fd_iso_step_static()

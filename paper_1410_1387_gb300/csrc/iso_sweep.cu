@@ -84,10 +84,12 @@ struct IsoCfg {
 // arguments).  Returns -1 to every thread when n >= n_end (a finished shot in a
 // batch: its CTAs do nothing).
 // step_take is the part of one thread; step_prologue shares its result with the CTA.
-__device__ __forceinline__ int step_take(DevState *st, unsigned ncta, int n_end)
+// With hold the time index is only read (a part of a step that another part completes).
+__device__ __forceinline__ int step_take(DevState *st, unsigned ncta, int n_end, bool hold = false)
 {
     int n = *reinterpret_cast<volatile int *>(&st->step);
     if (n >= n_end) return -1;
+    if (hold) return n;
     __threadfence();
     if (atomicAdd(&st->done, 1u) == ncta - 1) {
         st->done = 0;
@@ -197,8 +199,8 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 
     const int tid = threadIdx.x;
     const int x0 = bx * TX, y0 = by * TY;
-    const int z0 = bz * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, a.nz);
+    const int z0 = a.zb + bz * a.zchunk;             // planes [zb, nz - ztop) of this launch
+    const int z1 = min(z0 + a.zchunk, a.nz - a.ztop);
 
     if (tid == 0) {
         for (int s = 0; s < C::NA; ++s) {
@@ -230,7 +232,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
         // time index, u^n and the tables (a preceding kernel may have written
         // them) must be that step's.
         griddep_wait();
-        if (tid == 0) sh[0] = step_take(a.st, a.ncta, 0x7fffffff);
+        if (tid == 0) sh[0] = step_take(a.st, a.ncta, 0x7fffffff, a.hold != 0);
     }
     float *sgz = reinterpret_cast<float *>(smem_raw + C::OFF_GZ);   // z damping factors of the chunk
     for (int i = tid; i < z1 - z0; i += C::NT) sgz[i] = a.gz[z0 + i];
@@ -686,7 +688,9 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     IsoArgs a = a0;
-    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
+    const int zn = a.nz - a.ztop - a.zb;   // planes of this launch
+    if (zn <= 0) return cudaErrorInvalidValue;
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (zn + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
     const int smem = cmax(C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4), C::SMEM_FLOOR);
     // Programmatic stream serialisation: consecutive steps overlap one CTA's

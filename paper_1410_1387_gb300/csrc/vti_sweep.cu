@@ -68,8 +68,8 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, a.nz);
+    const int z0 = a.zb + blockIdx.z * a.zchunk;     // planes [zb, nz - ztop) of this launch
+    const int z1 = min(z0 + a.zchunk, a.nz - a.ztop);
 
     if (tid == 0) {
         for (int s = 0; s < C::NA; ++s) {
@@ -82,8 +82,9 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
         }
         fence_mbar_init();
         const int n = *reinterpret_cast<volatile int *>(&a.st->step);
+        // the last CTA advances the time index, unless a later part of the step will
         __threadfence();
-        if (atomicAdd(&a.st->done, 1u) == a.ncta - 1) {
+        if (!a.hold && atomicAdd(&a.st->done, 1u) == a.ncta - 1) {
             a.st->done = 0;
             *reinterpret_cast<volatile int *>(&a.st->step) = n + 1;
             __threadfence();
@@ -333,7 +334,9 @@ static cudaError_t launch_vt(const VtiMaps &tm, const VtiArgs &a0, cudaStream_t 
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     VtiArgs a = a0;
-    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);
+    const int zn = a.nz - a.ztop - a.zb;   // planes of this launch
+    if (zn <= 0) return cudaErrorInvalidValue;
+    dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (zn + a.zchunk - 1) / a.zchunk);
     a.ncta = grid.x * grid.y * grid.z;
     vti_sweep_kernel<RXY, RZ, TX, TY, LA>
         <<<grid, C::NT, C::SMEM, s>>>(tm.p, tm.q, tm.pp, tm.qp, tm.kx, tm.kn, tm.kz, a);

@@ -41,7 +41,7 @@ EXPORTS = [
     "fd_batch_create", "fd_batch_set_launch", "fd_batch_set_graph", "fd_batch_add", "fd_batch_remove",
     "fd_batch_steps_left", "fd_batch_run", "fd_batch_destroy",
     "fd_set_injection", "fd_adjoint_source", "fd_grad_accumulate",
-    "fd_set_z_window", "fd_halo_exchange", "fd_optimized_weights", "fd_set_weights",
+    "fd_set_z_window", "fd_halo_exchange", "fd_step_planes", "fd_optimized_weights", "fd_set_weights",
     "fd_debug_skip_copy",
 ]
 
@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
             "fd_grad_accumulate": [_vp, _vp, _vp, _vp],
             "fd_set_z_window": [_vp, _i, _i],
             "fd_halo_exchange": [_vp, _vp, _i],
+            "fd_step_planes": [_vp, _i, _i, _i],
             "fd_optimized_weights": [_i, _d, _vp],
             "fd_set_weights": [_vp, _vp, _vp],
             "fd_debug_skip_copy": [_vp, _i],
@@ -313,6 +314,10 @@ def fd_halo_exchange(lower, upper, planes: int) -> None:
     _check(lib().fd_halo_exchange(lower, upper, planes))
 
 
+def fd_step_planes(g, k_begin: int, k_end: int, complete: bool) -> None:
+    _check(lib().fd_step_planes(g, k_begin, k_end, int(bool(complete))))
+
+
 def fd_batch_create(stream: int) -> int:
     out = _vp()
     _check(lib().fd_batch_create(stream, ctypes.byref(out)))
@@ -434,6 +439,11 @@ class Grid:
     def run(self, nsteps: int):
         with self.torch.cuda.device(self.device):
             fd_run(self.h, nsteps)
+
+    def step_planes(self, k_begin: int, k_end: int, complete: bool):
+        """Part of a step: planes [k_begin, k_end) (see fd_step_planes)."""
+        with self.torch.cuda.device(self.device):
+            fd_step_planes(self.h, k_begin, k_end, complete)
 
     def set_graph(self, steps: int):
         fd_set_graph(self.h, steps)

@@ -8,10 +8,14 @@ not depend on the grid it sits in).  The damping layer follows the whole
 column (``fd_set_z_window``); the source and the receivers belong to the slab
 that owns their plane.
 
-``SlabShot`` runs all slabs of one shot on one GPU, the exchange done by the
-library (``fd_halo_exchange``: device-to-device copies on the slabs' stream).
-``RankSlab`` is one slab per process (one per GPU), the same planes sent point
-to point between neighbouring ranks by ``dist.halo_exchange``.
+Each step updates only the planes a slab owns (``fd_step_planes``): its ghost
+planes would be overwritten by the exchange anyway.  ``SlabShot`` runs all
+slabs of one shot on one GPU, the exchange done by the library
+(``fd_halo_exchange``: device-to-device copies on the slabs' stream).
+``RankSlab`` is one slab per process (one per GPU): it updates the owned
+planes next to each cut first, posts their point-to-point exchange with the
+neighbouring ranks (``dist.halo_exchange_start``), updates its interior while
+the planes are in flight, then waits for the exchange.
 """
 from __future__ import annotations
 
@@ -49,6 +53,26 @@ def slab_bounds(nz: int, nslabs: int, halo: int) -> list[Slab]:
         out.append(Slab(a, b, a - halo if s > 0 else 0, b + halo if s < nslabs - 1 else nz))
         a = b
     return out
+
+
+def step_parts(sl: Slab, halo: int, lower: bool, upper: bool):
+    """The owned planes of slab `sl` (local indices) as (boundary parts, interior
+    part): the planes next to a cut that has a neighbour, which the neighbour
+    needs as ghost planes, and the rest.  Boundary parts that would overlap
+    merge; the interior may be empty (None)."""
+    a, b = sl.a - sl.lo, sl.b - sl.lo
+    bnd = []
+    if lower:
+        bnd.append([a, a + halo])
+    if upper:
+        if bnd and bnd[-1][1] >= b - halo:
+            bnd[-1][1] = b
+        else:
+            bnd.append([b - halo, b])
+    lo_i = a + (halo if lower else 0)
+    hi_i = b - (halo if upper else 0)
+    interior = (lo_i, hi_i) if hi_i > lo_i else None
+    return [tuple(x) for x in bnd], interior
 
 
 def z_halo(shot) -> int:
@@ -103,10 +127,11 @@ class SlabShot:
             self.rec_keep.append(keep)
 
     def run(self, nsteps: int) -> None:
-        """nsteps steps: every slab steps, then each cut exchanges its ghost planes."""
+        """nsteps steps: every slab updates its own planes, then each cut
+        exchanges its ghost planes."""
         for _ in range(nsteps):
-            for g in self.grids:
-                g.run(1)
+            for g, sl in zip(self.grids, self.bounds):
+                g.step_planes(sl.a - sl.lo, sl.b - sl.lo, True)
             for s in range(len(self.grids) - 1):
                 fd.fd_halo_exchange(self.grids[s].h, self.grids[s + 1].h, self.halo)
 
@@ -160,10 +185,20 @@ class RankSlab:
             g.set_receivers(part.receivers, shot.nsteps if nt_cap is None else nt_cap)
 
     def run(self, nsteps: int) -> None:
+        """nsteps steps, each: the owned planes next to the cuts, then their
+        exchange posted, then the interior while the planes are in flight."""
         lower = self.rank - 1 if self.rank > 0 else None
         upper = self.rank + 1 if self.rank < self.world - 1 else None
-        fields = (0, 2) if self.shot.mode == "vti" else (0,)
+        bnd, interior = step_parts(self.sl, self.halo, lower is not None, upper is not None)
+        parts = bnd + ([interior] if interior else [])
+        # the buffers the step writes: the stored older levels (ISO: u; VTI: p, q)
+        fields = (1, 3) if self.shot.mode == "vti" else (1,)
         for _ in range(nsteps):
-            self.grid.run(1)
-            for f in fields:
-                fdist.halo_exchange(self.grid.field_view(f), self.halo, lower, upper)
+            new = [self.grid.field_view(f) for f in fields]
+            for i, (k0, k1) in enumerate(bnd):
+                self.grid.step_planes(k0, k1, i == len(parts) - 1)
+            posted = [fdist.halo_exchange_start(v, self.halo, lower, upper) for v in new]
+            if interior:
+                self.grid.step_planes(interior[0], interior[1], True)
+            for p in posted:
+                p.wait()

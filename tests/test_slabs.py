@@ -183,3 +183,23 @@ def test_oracle_slabs_over_gloo_match_the_unsplit_run(O, R, world):
             tr[:, o[4]] = o[5]
     assert np.array_equal(tr, tr_ref)
     assert np.abs(u_ref).max() > 0
+
+
+def test_step_parts_cover_the_owned_planes():
+    """The parts of a slab's step: boundary parts next to each cut that has a
+    neighbour (what the neighbour needs as ghosts), the interior, disjoint and
+    together exactly the owned planes; no part for the ghost planes."""
+    for nz, S, P in [(80, 3, 4), (24, 3, 4), (16, 2, 8), (9, 1, 4), (512, 8, 4), (25, 3, 4)]:
+        for s, sl in enumerate(slabs.slab_bounds(nz, S, P)):
+            lower, upper = s > 0, s < S - 1
+            bnd, interior = slabs.step_parts(sl, P, lower, upper)
+            parts = bnd + ([interior] if interior else [])
+            planes = sorted(k for k0, k1 in parts for k in range(k0, k1))
+            assert planes == list(range(sl.a - sl.lo, sl.b - sl.lo))        # each owned plane once
+            need = set()
+            if lower:
+                need |= set(range(sl.a - sl.lo, sl.a - sl.lo + P))
+            if upper:
+                need |= set(range(sl.b - sl.lo - P, sl.b - sl.lo))
+            assert {k for k0, k1 in bnd for k in range(k0, k1)} == need        # boundary parts: exactly those
+            assert all(k1 > k0 for k0, k1 in parts)
