@@ -101,8 +101,8 @@ def test_step_in_parts_equals_the_whole_step(fd, mode):
         R = 4 if mode == "iso4" else 8
         rec = np.array([[3, 4, 30], [20, 21, 5], [33, 2, 17], [7, 40, 44]], np.int32)   # gathered (not a lattice)
         shot = iso_shot(41, 44, 52, R, 12, seed=9, nb=5, src=(20, 21, 25), receivers=rec)
-    whole = fd.grid_from_shot(shot, device="cuda:0")
-    parts = fd.grid_from_shot(shot, device="cuda:0")
+    whole = fd.grid_from_shot(shot, device="cuda:0", nt_cap=shot.nsteps + 1)    # one more step below
+    parts = fd.grid_from_shot(shot, device="cuda:0", nt_cap=shot.nsteps + 1)
     nz = shot.nz
     cuts = [(17, 31), (0, 17), (31, nz)]            # out of order; the source plane inside one part
     for n in range(shot.nsteps):
