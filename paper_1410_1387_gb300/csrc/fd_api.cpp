@@ -796,10 +796,10 @@ int fd_set_graph(fd_grid_t *g, int steps)
 
 int fd_step_planes(fd_grid_t *g, int k_begin, int k_end, int complete)
 {
+    if (g && (k_begin < 0 || k_end > g->d.nz || k_begin >= k_end))
+        return fail(FD_ERR_INVALID_ARG, "planes [%d, %d) are not a non-empty range of 0..%d", k_begin, k_end, g->d.nz);
     int rc = check_ready(g, 1);
     if (rc) return rc;
-    if (k_begin < 0 || k_end > g->d.nz || k_begin >= k_end)
-        return fail(FD_ERR_INVALID_ARG, "planes [%d, %d) are not a non-empty range of 0..%d", k_begin, k_end, g->d.nz);
     cudaError_t e = enqueue_part(g, g->cur, k_begin, g->d.nz - k_end, complete ? 0 : 1, g->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
     if (complete) {
