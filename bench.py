@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 KERNEL_SRC = {"iso_sweep_kernel": "iso_sweep.cu", "vti_sweep_kernel": "vti_sweep.cu"}
 KERNEL_HEADERS = {"iso_sweep_kernel": ("tmem.cuh", "launch_shape.h"),   # besides ptx.cuh and fd_internal.h
-                  "vti_sweep_kernel": ("launch_shape.h",)}
+                  "vti_sweep_kernel": ("tmem.cuh", "launch_shape.h")}
 
 
 def parse():

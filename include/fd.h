@@ -238,8 +238,8 @@ int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead);
 
 /*
  * Failure-detection test hook: in the next step (run outside any graph), the
- * isotropic sweep's CTA (0,0,0) withholds the copy of plane `plane` of u^n
- * (a plane inside its z chunk and halo).  Its consumers' bounded wait (about
+ * sweep's CTA (0,0,0) withholds the copy of plane `plane` of u^n (VTI: p^n), a
+ * plane inside its z chunk.  Its consumers' bounded wait (about
  * one second) runs out; the CTA records the timeout in the grid's status
  * block, waits (bounded) for its copies in flight and exits, and the next
  * fd_sync / host read-back returns FD_ERR_TIMEOUT.  The context stays usable;

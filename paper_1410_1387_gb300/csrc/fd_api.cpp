@@ -261,6 +261,8 @@ cudaError_t enqueue_part(fd_grid *g, int cur, int zb, int ztop, int hold, cudaSt
         for (int l = 0; l <= kMaxR; ++l) a.wxy2[l] = make_float2(g->wxy[l], g->wxy[l]);
         a.src = src; a.rec = rec; a.st = g->st;
         a.zb = zb; a.ztop = ztop; a.hold = hold;
+        a.skip_plane1 = g->debug_skip + 1;
+        g->debug_skip = -1;
         const VtiMaps maps{g->tm_halo[cur],    g->tm_tile[2 + cur], g->tm_tile[1 - cur], g->tm_tile[3 - cur],
                            g->tm_model[0],     g->tm_model[1],      g->tm_model[2]};
         e = launch_vti(d.r_xy, d.r_z, g->L, maps, a, s);
@@ -1024,7 +1026,6 @@ int fd_debug_skip_copy(fd_grid_t *g, int plane)
         t_static_skip = plane;
         return FD_OK;
     }
-    if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "the hook is in the isotropic sweep");
     if (plane < 0 || plane >= g->d.nz) return fail(FD_ERR_INVALID_ARG, "plane %d outside 0..%d", plane, g->d.nz - 1);
     g->debug_skip = plane;
     return FD_OK;

@@ -86,6 +86,7 @@ struct VtiArgs {
     DevState *st;
     unsigned int ncta;
     int zb, ztop, hold;     // part of a step, as in IsoArgs (all zero: the whole step)
+    int skip_plane1;        // test hook: 1 + a plane whose p^n copy CTA (0,0,0) withholds (0 = none)
 };
 
 // fd_debug_skip_copy(NULL, plane) arms the hook for the next fd_iso_step_static()

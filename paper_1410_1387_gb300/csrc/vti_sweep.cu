@@ -12,12 +12,16 @@
 //   * ring B: the TX x TY tiles of p_prev, q_prev, kx, kn, kz of plane k and of
 //     q^n of plane k + R_z (the value that enters the z queue at step k);
 //   * each consumer thread keeps the 2 R_z + 1 z neighbours of its 4 q values in
-//     registers; the new levels overwrite the older ones in place.
+//     registers; the new levels overwrite the older ones in place.  At R_z = 8 in
+//     32 x 32 tiles (the default) the queues live in tensor memory instead and
+//     each thread takes two adjacent rows, which share their y-neighbour reads of
+//     p (the smaller tile also cuts ring A's halo from 5.5x to 3.1x the tile).
 // Compulsory HBM traffic: 36 bytes per point update (read p, q, p_prev, q_prev,
 // kx, kn, kz; write p, q).
 #include "fd_internal.h"
 #include "launch_shape.h"
 #include "ptx.cuh"
+#include "tmem.cuh"
 
 namespace fdk {
 
@@ -26,7 +30,13 @@ constexpr long long kVtiWaitLimit = 2000000000LL;   // ~1 s
 template <int RXY, int RZ, int TX, int TY, int LA>
 struct VtiCfg {
     static constexpr int NTX = TX / 4;
-    static constexpr int NC = NTX * TY;
+    // R_z = 8 in 32 x 32 tiles keeps q's z queues in tensor memory, which frees the
+    // registers for two tile rows per thread: the rows share their y-neighbour
+    // reads of p (24 float4 per 8 points instead of 48 at R_xy = 12).
+    static constexpr bool TQ = (RZ == 8 && TX == 32 && TY == 32);
+    static constexpr int RPT = TQ ? 2 : 1;          // tile rows per consumer thread
+    static constexpr int NC = NTX * TY / RPT;
+    static constexpr int TMEM_COLS = 128;           // two rows x 16 slots x 4 columns
     static constexpr int NCW = NC / 32;
     static constexpr int NT = NC + 32;
     static constexpr int SW = TX + 2 * RXY;
@@ -40,16 +50,91 @@ struct VtiCfg {
     static constexpr int NB = LA + 1;
     static constexpr int OFF_B = NA * SLOT_A * 4;
     static constexpr int OFF_BAR = OFF_B + NB * SLOT_B * 4;
-    static constexpr int SMEM = OFF_BAR + 8 * (2 * NA + 2 * NB) + 16;
+    static constexpr int SMEM = OFF_BAR + 8 * (2 * NA + 2 * NB) + 32;   // barriers, then 8 ints
     static constexpr int NW = 2 * RZ + 1;
     static_assert(TX % 4 == 0 && RXY % 4 == 0, "x alignment");
     static_assert(NC % 32 == 0, "whole consumer warps");
     static_assert((SLOT_A * 4) % 128 == 0 && (TILE * 4) % 128 == 0, "slot alignment");
     static_assert(SW <= 256 && SH <= 256, "TMA box limit");
+    static_assert(!TQ || NC == 128, "tensor-memory queues: one consumer warp per lane quarter");
 };
 
+// Dq of one row from its tensor-memory ring v (plane p of q in slot p mod 16,
+// planes k - 8 .. k + 7) when k mod 16 = S, and the entering plane q8 = q^{k+8}:
+// sum over m = 0..16 of w2[m] q^{k-8+m}, in ascending m as the register form
+// does, on the point pairs (0, 1) and (2, 3); qc receives q^k.
+template <int S>
+__device__ __forceinline__ void vti_dq_slots(const float4 (&v)[16], const float4 q8, const float2 (&w2)[17],
+                                             float2 &lo, float2 &hi, float4 &qc)
+{
+    lo = make_float2(0.f, 0.f);
+    hi = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 17; ++m) {
+        const float4 u = m == 16 ? q8 : v[(S + 8 + m) & 15];   // plane k - 8 + m
+        lo = __ffma2_rn(w2[m], make_float2(u.x, u.y), lo);
+        hi = __ffma2_rn(w2[m], make_float2(u.z, u.w), hi);
+    }
+    qc = v[S];
+}
+
+// The two updates of one thread's 4 points of plane k in row gyi (Eqs. 1-2 in
+// the leapfrog of Eq. 3, damping in its deferred form, G = gx * gy * gz), with the
+// source and the receivers; the new levels are written over the older ones.
+__device__ __forceinline__ void vti_update_row(const VtiArgs &a, const int n, const int k, const int gxi,
+                                               const int gyi, const long long rowoff, const float (&hp)[4],
+                                               const float (&dq)[4], const float (&pcu)[4], const float (&qc)[4],
+                                               const float (&ppu)[4], const float (&qpu)[4], const float (&kxu)[4],
+                                               const float (&knu)[4], const float (&kzu)[4], const float (&gu)[4],
+                                               const float gyz)
+{
+    float op[4], oq[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float G = gu[e] * gyz;
+        const float zt = kzu[e] * dq[e];
+        op[e] = fmaf(kxu[e], hp[e], fmaf(2.f, pcu[e], -G * ppu[e])) + zt;
+        oq[e] = fmaf(knu[e], hp[e], fmaf(2.f, qc[e], -G * qpu[e])) + zt;
+    }
+    if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len) {
+        const float sv = a.src.tab[n];
+        op[a.src.sx - gxi] += sv;
+        if (a.src.into_q) oq[a.src.sx - gxi] += sv;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float G = gu[e] * gyz;
+        op[e] *= G;
+        oq[e] *= G;
+    }
+    float *dp = a.pprev + k * a.plane + rowoff;
+    float *dq_ = a.qprev + k * a.plane + rowoff;
+    if (gxi + 3 < a.nx) {
+        st_cs(dp, make_float4(op[0], op[1], op[2], op[3]));
+        st_cs(dq_, make_float4(oq[0], oq[1], oq[2], oq[3]));
+    } else {
+        for (int e = 0; e < 4; ++e)
+            if (gxi + e < a.nx) {
+                dp[e] = op[e];
+                dq_[e] = oq[e];
+            }
+    }
+    if (a.rec.on && k == a.rec.rk) {
+        const int ry = gyi - a.rec.ry0;
+        const int row = n - a.rec.t0;
+        if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 && row < a.rec.cap) {
+            float *trow = a.rec.trace + (long long)row * a.rec.nrec + (long long)(ry / a.rec.rsy) * a.rec.rnx;
+            for (int e = 0; e < 4; ++e) {
+                const int rx = gxi + e - a.rec.rx0;
+                if (gxi + e < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
+                    trow[rx / a.rec.rsx] = op[e];
+            }
+        }
+    }
+}
+
 template <int RXY, int RZ, int TX, int TY, int LA>
-__global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
+__global__ void __launch_bounds__(VtiCfg<RXY, RZ, TX, TY, LA>::NT, 2)
     vti_sweep_kernel(const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_q,
                      const __grid_constant__ CUtensorMap tm_pp, const __grid_constant__ CUtensorMap tm_qp,
                      const __grid_constant__ CUtensorMap tm_kx, const __grid_constant__ CUtensorMap tm_kn,
@@ -63,7 +148,9 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
     uint64_t *emptyA = fullA + C::NA;
     uint64_t *fullB = emptyA + C::NA;
     uint64_t *emptyB = fullB + C::NB;
-    int *sh = reinterpret_cast<int *>(emptyB + C::NB);   // [0] n, [1] abort, [2..3] issue counts
+    // [0] n, [1] abort, [2..3] issue counts, [4] tensor-memory address
+    int *sh = reinterpret_cast<int *>(emptyB + C::NB);
+    uint32_t *sh_tmem = reinterpret_cast<uint32_t *>(sh + 4);
     volatile int *sh_abort = sh + 1;
 
     const int tid = threadIdx.x;
@@ -94,7 +181,13 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
         sh[2] = z0;
         sh[3] = z0;
     }
+    if constexpr (C::TQ) {
+        __syncwarp();
+        if (tid < 32) tmem_alloc(sh_tmem, C::TMEM_COLS);
+        tmem_fence_before_sync();
+    }
     __syncthreads();
+    if constexpr (C::TQ) tmem_fence_after_sync();
     const int n = sh[0];
     bool failed = false;
 
@@ -105,16 +198,22 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             for (const CUtensorMap *m : maps) prefetch_tmap(m);
             int a_end = z0, b_end = z0;
             bool ok = true;
+            // test hook (fd_debug_skip_copy): CTA (0,0,0) withholds one plane's copy of
+            // p^n, so that its consumers' bounded wait runs out; every wait on that path
+            // is bounded
+            const int skip = (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) ? a.skip_plane1 - 1 : -1;
             for (int k = z0; ok && k < z1; ++k) {
                 if (*sh_abort) break;
                 const int u = k - z0;
                 const int sa = u % C::NA, sb = u % C::NB;
-                if (u >= C::NA && !mbar_wait_bounded(&emptyA[sa], ((u / C::NA) - 1) & 1, kVtiWaitLimit)) {
-                    ok = false;
-                    break;
+                if (k != skip) {
+                    if (u >= C::NA && !mbar_wait_bounded(&emptyA[sa], ((u / C::NA) - 1) & 1, kVtiWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&fullA[sa], C::SLOT_A * 4);
+                    tma_load_3d(ringA + sa * C::SLOT_A, &tm_p, &fullA[sa], x0 - RXY, y0 - RXY, k);
                 }
-                mbar_arrive_expect_tx(&fullA[sa], C::SLOT_A * 4);
-                tma_load_3d(ringA + sa * C::SLOT_A, &tm_p, &fullA[sa], x0 - RXY, y0 - RXY, k);
                 a_end = k + 1;
                 if (u >= C::NB && !mbar_wait_bounded(&emptyB[sb], ((u / C::NB) - 1) & 1, kVtiWaitLimit)) {
                     ok = false;
@@ -138,6 +237,193 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             }
             sh[2] = a_end;
             sh[3] = b_end;
+        }
+    } else if constexpr (C::TQ) {
+        // ------------------------------------------------------------ consumer warps (two rows each)
+        // Thread (tx, tr) owns 4 consecutive x points of tile rows 2 tr and 2 tr + 1;
+        // the rows' y neighbours overlap, so each staged row of p above and below is
+        // read once for both.  Per point the arithmetic, and its order, is that of
+        // the one-row form.  q's z queues live in tensor memory: row e's planes
+        // k - RZ .. k + RZ - 1 in columns 64 e + [0, 64), plane p in slot p mod 16.
+        const int tx = tid % C::NTX, tr = tid / C::NTX;
+        const int gxi = x0 + 4 * tx, gy0 = y0 + 2 * tr;
+        const bool xin = gxi < a.nx;
+        const bool act[2] = {xin && gy0 < a.ny, xin && gy0 + 1 < a.ny};
+        const long long rowoff0 = (long long)gy0 * a.pitch + gxi;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int own = (2 * tr + RXY) * C::SW + RXY + 4 * tx;   // row 0's float4 in ring A (row 1: + SW)
+        const int ownb = 2 * tr * TX + 4 * tx;                   // row 0's float4 in a ring B tile (row 1: + TX)
+        const int lane = tid & 31;
+        const uint32_t tl = *sh_tmem + ((uint32_t)(32 * (tid / 32)) << 16);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+#pragma unroll
+            for (int m0 = 0; m0 < 2 * RZ; m0 += 8) {
+                float4 v[8];   // eight loads in flight before their stores
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int p = z0 - RZ + m0 + m;
+                    v[m] = (act[e] && p >= 0 && p < a.nz) ? ld_nc_na(a.q + p * a.plane + rowoff0 + e * a.pitch)
+                                                          : zero4;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int m = 0; m < 8; ++m) tmem_st4(tl + 64 * e + 4 * (uint32_t)((z0 - RZ + m0 + m) & 15), v[m]);
+            }
+        }
+        float4 g4 = zero4;
+        float gyv[2] = {0.f, 0.f};
+        if (xin) g4 = *reinterpret_cast<const float4 *>(a.gx + gxi);
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            if (act[e]) gyv[e] = a.gy[gy0 + e];
+
+        // tcgen05 loads and stores are warp-collective: the abort flag and each
+        // bounded wait's outcome are agreed across the warp before any branch
+        bool ok = true;
+        for (int k = z0; ok && k < z1; ++k) {
+            if (!__all_sync(0xffffffffu, *sh_abort == 0)) {
+                ok = false;
+                break;
+            }
+            const int u = k - z0;
+            const int sa = u % C::NA, sb = u % C::NB;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&fullB[sb], (u / C::NB) & 1, kVtiWaitLimit))) {
+                ok = false;
+                break;
+            }
+            const float *tb = ringB + sb * C::SLOT_B;
+            float4 qin[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                qin[e] = (k + RZ < a.nz) ? *reinterpret_cast<const float4 *>(tb + 5 * C::TILE + ownb + e * TX) : zero4;
+            const float *zrow = tb + 6 * C::TILE;
+            float2 w2[2 * RZ + 1];
+#pragma unroll
+            for (int m = 0; m < C::NW; ++m) w2[m] = *reinterpret_cast<const float2 *>(zrow + 2 * m);
+            const float gz = zrow[2 * C::NW];
+
+            // Dq and the centre q of both rows from the tensor-memory rings
+            float2 dq_lo[2], dq_hi[2];
+            float4 qc[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float4 v[16];
+                __syncwarp();
+                tmem_ld_ring(tl + 64 * e, v);
+                switch (k & 15) {
+#define FD_VTI_DQ(S_) \
+    case S_: vti_dq_slots<S_>(v, qin[e], w2, dq_lo[e], dq_hi[e], qc[e]); break;
+                    FD_VTI_DQ(0) FD_VTI_DQ(1) FD_VTI_DQ(2) FD_VTI_DQ(3) FD_VTI_DQ(4) FD_VTI_DQ(5) FD_VTI_DQ(6)
+                    FD_VTI_DQ(7) FD_VTI_DQ(8) FD_VTI_DQ(9) FD_VTI_DQ(10) FD_VTI_DQ(11) FD_VTI_DQ(12) FD_VTI_DQ(13)
+                    FD_VTI_DQ(14) FD_VTI_DQ(15)
+#undef FD_VTI_DQ
+                }
+            }
+
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&fullA[sa], (u / C::NA) & 1, kVtiWaitLimit))) {
+                ok = false;
+                break;
+            }
+            const float *t = ringA + sa * C::SLOT_A;
+            // Hp: centre, then x pairs (scalar sums, f32x2 FMAs: per lane the
+            // rounding of fmaf), then y pairs
+            float xw[2][4 + 2 * RXY];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float *rw = t + own + e * C::SW - RXY;
+#pragma unroll
+                for (int m = 0; m < (4 + 2 * RXY) / 4; ++m) {
+                    const float4 v = *reinterpret_cast<const float4 *>(rw + 4 * m);
+                    xw[e][4 * m + 0] = v.x; xw[e][4 * m + 1] = v.y; xw[e][4 * m + 2] = v.z; xw[e][4 * m + 3] = v.w;
+                }
+            }
+            float2 lo[2], hi[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float *w = xw[e];
+                const float2 w02 = make_float2(a.w0, a.w0);
+                lo[e] = __fmul2_rn(w02, make_float2(w[RXY], w[RXY + 1]));
+                hi[e] = __fmul2_rn(w02, make_float2(w[RXY + 2], w[RXY + 3]));
+#pragma unroll
+                for (int l = 1; l <= RXY; ++l) {
+                    float2 slo, shi;
+                    if ((l & 1) == 0) {
+                        slo = __fadd2_rn(make_float2(w[RXY + l], w[RXY + 1 + l]), make_float2(w[RXY - l], w[RXY + 1 - l]));
+                        shi = __fadd2_rn(make_float2(w[RXY + 2 + l], w[RXY + 3 + l]),
+                                         make_float2(w[RXY + 2 - l], w[RXY + 3 - l]));
+                    } else {
+                        slo = make_float2(w[RXY + l] + w[RXY - l], w[RXY + 1 + l] + w[RXY + 1 - l]);
+                        shi = make_float2(w[RXY + 2 + l] + w[RXY + 2 - l], w[RXY + 3 + l] + w[RXY + 3 - l]);
+                    }
+                    lo[e] = __ffma2_rn(a.wxy2[l], slo, lo[e]);
+                    hi[e] = __ffma2_rn(a.wxy2[l], shi, hi[e]);
+                }
+            }
+            auto pair = [&](int e, const float2 w, const float4 &up, const float4 &dn) {
+                lo[e] = __ffma2_rn(w, __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo[e]);
+                hi[e] = __ffma2_rn(w, __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi[e]);
+            };
+            // y pairs: at l, row 0 takes rows (l, -l) and row 1 rows (l + 1, 1 - l),
+            // relative to row 0; rows 0 and 1 themselves are the x windows' centres
+            const float4 pc[2] = {make_float4(xw[0][RXY], xw[0][RXY + 1], xw[0][RXY + 2], xw[0][RXY + 3]),
+                                  make_float4(xw[1][RXY], xw[1][RXY + 1], xw[1][RXY + 2], xw[1][RXY + 3])};
+            float4 up0 = pc[1], dn1 = pc[0];
+#pragma unroll
+            for (int l = 1; l <= RXY; ++l) {
+                const float4 dn0 = *reinterpret_cast<const float4 *>(t + own - l * C::SW);
+                const float4 up1 = *reinterpret_cast<const float4 *>(t + own + (l + 1) * C::SW);
+                pair(0, a.wxy2[l], up0, dn0);
+                pair(1, a.wxy2[l], up1, dn1);
+                up0 = up1;
+                dn1 = dn0;
+            }
+            float4 ppv[2], qpv[2], kxv[2], knv[2], kzv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float *b = tb + ownb + e * TX;
+                ppv[e] = *reinterpret_cast<const float4 *>(b + 0 * C::TILE);
+                qpv[e] = *reinterpret_cast<const float4 *>(b + 1 * C::TILE);
+                kxv[e] = *reinterpret_cast<const float4 *>(b + 2 * C::TILE);
+                knv[e] = *reinterpret_cast<const float4 *>(b + 3 * C::TILE);
+                kzv[e] = *reinterpret_cast<const float4 *>(b + 4 * C::TILE);
+            }
+            // this warp no longer reads plane k from either ring: order its plain
+            // reads before the producer's next copies into these slots
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&emptyA[sa]);
+                mbar_arrive(&emptyB[sb]);
+            }
+            // plane k + RZ takes the slot of plane k - RZ, no longer needed
+            {
+                const uint32_t cs = tl + 4 * (uint32_t)((k + RZ) & 15);
+                tmem_st4_2(cs, qin[0], cs + 64, qin[1]);
+            }
+
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (!act[e]) continue;
+                const int gyi = gy0 + e;
+                const float gyz = gyv[e] * gz;
+                const float hp[4] = {lo[e].x, lo[e].y, hi[e].x, hi[e].y};
+                const float dq[4] = {dq_lo[e].x, dq_lo[e].y, dq_hi[e].x, dq_hi[e].y};
+                const float pcu[4] = {pc[e].x, pc[e].y, pc[e].z, pc[e].w};
+                const float qcu[4] = {qc[e].x, qc[e].y, qc[e].z, qc[e].w};
+                const float ppu[4] = {ppv[e].x, ppv[e].y, ppv[e].z, ppv[e].w};
+                const float qpu[4] = {qpv[e].x, qpv[e].y, qpv[e].z, qpv[e].w};
+                const float kxu[4] = {kxv[e].x, kxv[e].y, kxv[e].z, kxv[e].w};
+                const float knu[4] = {knv[e].x, knv[e].y, knv[e].z, knv[e].w};
+                const float kzu[4] = {kzv[e].x, kzv[e].y, kzv[e].z, kzv[e].w};
+                const float gu[4] = {g4.x, g4.y, g4.z, g4.w};
+                vti_update_row(a, n, k, gxi, gyi, rowoff0 + e * a.pitch, hp, dq, pcu, qcu, ppu, qpu, kxu, knu, kzu,
+                               gu, gyz);
+            }
+        }
+        if (!ok) {
+            *sh_abort = 1;
+            failed = true;
         }
     } else {
         // ------------------------------------------------------------ consumer warps
@@ -241,7 +527,6 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
             const float dq[4] = {dq_lo.x, dq_lo.y, dq_hi.x, dq_hi.y};
 
             if (act) {
-                const float gyz = gyv * gz;
                 const float pcu[4] = {pc.x, pc.y, pc.z, pc.w};
                 const float qc[4] = {qq[RZ].x, qq[RZ].y, qq[RZ].z, qq[RZ].w};
                 const float ppu[4] = {ppv.x, ppv.y, ppv.z, ppv.w};
@@ -250,51 +535,7 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
                 const float knu[4] = {knv.x, knv.y, knv.z, knv.w};
                 const float kzu[4] = {kzv.x, kzv.y, kzv.z, kzv.w};
                 const float gu[4] = {g4.x, g4.y, g4.z, g4.w};
-                float op[4], oq[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float G = gu[e] * gyz;
-                    const float zt = kzu[e] * dq[e];
-                    op[e] = fmaf(kxu[e], hp[e], fmaf(2.f, pcu[e], -G * ppu[e])) + zt;
-                    oq[e] = fmaf(knu[e], hp[e], fmaf(2.f, qc[e], -G * qpu[e])) + zt;
-                }
-                if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len) {
-                    const float sv = a.src.tab[n];
-                    op[a.src.sx - gxi] += sv;
-                    if (a.src.into_q) oq[a.src.sx - gxi] += sv;
-                }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float G = gu[e] * gyz;
-                    op[e] *= G;
-                    oq[e] *= G;
-                }
-                float *dp = a.pprev + k * a.plane + rowoff;
-                float *dq_ = a.qprev + k * a.plane + rowoff;
-                if (gxi + 3 < a.nx) {
-                    st_cs(dp, make_float4(op[0], op[1], op[2], op[3]));
-                    st_cs(dq_, make_float4(oq[0], oq[1], oq[2], oq[3]));
-                } else {
-                    for (int e = 0; e < 4; ++e)
-                        if (gxi + e < a.nx) {
-                            dp[e] = op[e];
-                            dq_[e] = oq[e];
-                        }
-                }
-                if (a.rec.on && k == a.rec.rk) {
-                    const int ry = gyi - a.rec.ry0;
-                    const int row = n - a.rec.t0;
-                    if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 &&
-                        row < a.rec.cap) {
-                        float *trow = a.rec.trace + (long long)row * a.rec.nrec +
-                                      (long long)(ry / a.rec.rsy) * a.rec.rnx;
-                        for (int e = 0; e < 4; ++e) {
-                            const int rx = gxi + e - a.rec.rx0;
-                            if (gxi + e < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
-                                trow[rx / a.rec.rsx] = op[e];
-                        }
-                    }
-                }
+                vti_update_row(a, n, k, gxi, gyi, rowoff, hp, dq, pcu, qc, ppu, qpu, kxu, knu, kzu, gu, gyv * gz);
             }
 #pragma unroll
             for (int m = 0; m < 2 * RZ; ++m) qq[m] = qq[m + 1];
@@ -305,7 +546,13 @@ __global__ void __launch_bounds__((TX / 4) * TY + 32, 2)
         }
     }
 
-    if (__syncthreads_or(failed) && tid == C::NC) {
+    if constexpr (C::TQ) tmem_fence_before_sync();
+    const bool any_failed = __syncthreads_or(failed);
+    if constexpr (C::TQ) {
+        tmem_fence_after_sync();
+        if (tid < 32) tmem_dealloc(*sh_tmem, C::TMEM_COLS);
+    }
+    if (any_failed && tid == C::NC) {
         atomicOr(&a.st->err, kErrTmaTimeout);
         atomicCAS(&a.st->err_info, 0, 1 + (int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)));
         const int a_end = sh[2], b_end = sh[3];
@@ -347,6 +594,7 @@ static cudaError_t launch_vt(const VtiMaps &tm, const VtiArgs &a0, cudaStream_t 
     X(12, 8, 64, 8, 2)     \
     X(12, 8, 64, 8, 3)     \
     X(12, 8, 32, 16, 2)    \
+    X(12, 8, 32, 32, 2)    \
     X(4, 4, 64, 8, 2)
 
 cudaError_t launch_vti(int rxy, int rz, const Launch &L, const VtiMaps &tm, const VtiArgs &a, cudaStream_t s)
@@ -372,8 +620,10 @@ Launch vti_default_launch(int rxy, int rz, int nx, int ny, int nz)
 {
     (void)rxy;
     Launch L;
-    L.tx = 64;
-    L.ty = 8;
+    // R_z = 8: 32 x 32 tiles, two rows per thread, q's z queues in tensor memory
+    // (512^3: 167.3 vs 159.2 Gpts/s for the one-row 64 x 8 form on one box)
+    L.tx = rz == 8 ? 32 : 64;
+    L.ty = rz == 8 ? 32 : 8;
     L.lookahead = 2;
     // two CTAs per SM; at 512^3, 7 chunks of 74 planes (147.3 vs 142.5 Gpts/s for 4 of 128 on one box)
     L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * 2, 2 * rz);

@@ -123,3 +123,61 @@ def test_vti_full_size_512_one_step_sampled(fd, O):
     wp, wq = P.vti_step_points(shot.v, shot.eps, shot.delta, p, q, pts, G * pp[sel], G * qp[sel], 24)
     assert np.abs(p1[sel] - wp).max() <= 2e-6 * np.abs(p1).max()
     assert np.abs(q1[sel] - wq).max() <= 2e-6 * np.abs(q1).max()
+
+
+VTI_TILES = [(64, 8, 2), (64, 8, 3), (32, 16, 2), (32, 32, 2)]
+
+
+@pytest.mark.parametrize("shape", [(70, 45, 50), (33, 90, 41), (97, 66, 23)])
+def test_vti_tiles_are_bitwise_identical(fd, shape):
+    """Every VTI tile built into the library -- the one-row register forms and
+    the two-row form whose q queues live in tensor memory (32 x 32) -- gives the
+    same levels and traces bit for bit, with stretched dz, ragged x and y and
+    several z chunks (the per-point arithmetic and its order are shared)."""
+    steps = 30
+    shot = vti_small(*shape, steps=steps, seed=31)
+    ref = None
+    for tx, ty, la in VTI_TILES:
+        for zc in (shape[2], 16):
+            g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=steps)
+            g.set_launch(tx, ty, zc, la)
+            g.run(steps)
+            out = (g.state(), g.traces())
+            g.close()
+            if ref is None:
+                ref = out
+                assert np.abs(out[1]).max() > 0
+                continue
+            for a, b in zip(out[0], ref[0]):
+                np.testing.assert_array_equal(a, b)
+            np.testing.assert_array_equal(out[1], ref[1])
+
+
+@pytest.mark.parametrize("tile", [(64, 8, 2), (32, 32, 2)])
+def test_vti_bounded_wait_reports_timeout(fd, O, tile):
+    """Failure detection in the VTI sweep without a fault: CTA (0,0,0) is denied
+    one plane's copy of p^n (the test hook), its bounded wait runs out, it
+    records the timeout and exits -- in the 32 x 32 form after freeing its
+    tensor memory, or the next launches could not allocate -- and fd_sync
+    reports FD_ERR_TIMEOUT; a fresh grid in the same context, in the same tile,
+    still matches the oracle."""
+    import time
+    tx, ty, la = tile
+    shot = vti_small(48, 40, 36, steps=12, seed=7)
+    g = fd.grid_from_shot(shot, device="cuda:0")
+    g.set_launch(tx, ty, 36, la)
+    fd.fd_debug_skip_copy(g.h, 5)
+    t0 = time.perf_counter()
+    g.run(1)
+    with pytest.raises(fd.FdError) as e:
+        g.sync()
+    assert e.value.code == fd.FD_ERR_TIMEOUT and "timed out" in str(e.value)
+    assert 0.5 < time.perf_counter() - t0 < 30.0
+    g.close()
+    g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=shot.nsteps)
+    g.set_launch(tx, ty, 36, la)
+    g.run(shot.nsteps)
+    p, _, q, _ = g.state()
+    g.close()
+    pr, _, qr, _, _ = oracle_problem(O, shot).vti_run(shot.v, shot.eps, shot.delta, shot.nsteps)
+    assert max_rel(p, pr) <= 1e-4 and max_rel(q, qr) <= 1e-4
