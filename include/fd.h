@@ -190,6 +190,16 @@ int fd_step(fd_grid_t *g);
    fd_set_graph).  Checks all of them against the receiver buffer first. */
 int fd_run(fd_grid_t *g, int nsteps);
 
+/* One time step of g's operator (Eq. 3) between caller-owned levels: reads u^n
+   from cur and the stored older level from prev, writes u^{n+1} to out (device
+   arrays in g's pitched layout, 16-byte aligned; out may be prev -- the
+   in-place step -- but not cur).  g's model, damping layer, source and
+   receivers apply at g's time index, which advances; g's own levels are left
+   as they are.  Isotropic grids.  Lets a caller keep a run of consecutive
+   levels without copying them (the adjoint's recomputed segments).  Tensor
+   maps of these buffers are cached on g (by address). */
+int fd_step_from(fd_grid_t *g, const float *cur, const float *prev, float *out);
+
 /* Use replays of a CUDA graph of `steps` launches (even, 2..1024) in fd_run;
    0 = plain launches (the default). */
 int fd_set_graph(fd_grid_t *g, int steps);

@@ -8,13 +8,14 @@ For J = 1/2 sum_n sum_r (u^{n+1}(x_r) - dobs[n][r])^2 of an isotropic shot:
 * ``fd_adjoint_source`` turns the traces and data into the adjoint's injection
   rows (kappa(x_r) r, reversed in time) and J;
 * backward, segment by segment from the last: restore the checkpoint, recompute
-  the C forward levels u^n of the segment with ``fd_step`` (kept in a segment
-  buffer), then run the adjoint grid one step per level (the same sweep kernel,
+  the C forward levels u^n of the segment with ``fd_step_from`` (each written
+  straight into a segment buffer, no copies), then run the adjoint grid one
+  step per level (the same sweep kernel,
   fed by the injection lattice: z_n = G (2 z_{n+1} - G z_{n+2} + K L z_{n+1} +
   K R^T r_{n-1})) and accumulate dJ/dv += 2 dt z_{n+1} (L u^n) / sqrt(K) with
   ``fd_grad_accumulate``.
 
-Memory: 2 N/C checkpoint fields + C segment levels + 2 grids.
+Memory: 2 N/C checkpoint fields + C - 1 segment levels + 2 grids.
 """
 from __future__ import annotations
 
@@ -78,18 +79,20 @@ class AdjointSolver:
         fd.fd_set_injection(A.h, self.rec, self.nrec, inj, N)
         pitch = F.layout.pitch
         grad = torch.zeros((s.nz, s.ny, pitch), device=self.device)
-        seg = torch.empty((C, s.nz, s.ny, pitch), device=self.device)
+        seg = torch.empty((max(C - 1, 1), s.nz, s.ny, pitch), device=self.device)
         with torch.cuda.device(self.device):
             for n0, cur, prev in reversed(cps):
                 ln = min(C, N - n0)
                 fd.fd_set_state(F.h, cur, prev, ptr_kind=fd.FD_PTR_DEVICE, time_index=n0)
-                seg[0].copy_(F.field_view(0))
+                levels = [F.field_view(0)]             # u^{n0}, in F's own buffer
+                older = F.field_view(1)                # its stored older level
                 for j in range(1, ln):
-                    fd.fd_step(F.h)
-                    seg[j].copy_(F.field_view(0))
+                    fd.fd_step_from(F.h, levels[-1], older, seg[j - 1])
+                    older = levels[-1]
+                    levels.append(seg[j - 1])
                 for n in range(n0 + ln - 1, n0 - 1, -1):
                     fd.fd_step(A.h)                                   # z_{n+1}
-                    fd.fd_grad_accumulate(F.h, A.field_view(0), seg[n - n0], grad)
+                    fd.fd_grad_accumulate(F.h, A.field_view(0), levels[n - n0], grad)
         A.close()
         F.close()
         self._state = None

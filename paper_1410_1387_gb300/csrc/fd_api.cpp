@@ -786,6 +786,35 @@ int fd_grad_accumulate(fd_grid_t *g, const float *z, const float *a, float *grad
     return FD_OK;
 }
 
+int fd_step_from(fd_grid_t *g, const float *cur, const float *prev, float *out)
+{
+    int rc = check_ready(g, 1);
+    if (rc) return rc;
+    if (g->d.mode != FD_MODE_ISO) return fail(FD_ERR_UNSUPPORTED, "fd_step_from takes isotropic grids");
+    if (!cur || !prev || !out) return fail(FD_ERR_INVALID_ARG, "NULL field");
+    if ((reinterpret_cast<uintptr_t>(cur) | reinterpret_cast<uintptr_t>(prev) | reinterpret_cast<uintptr_t>(out)) % 16)
+        return fail(FD_ERR_INVALID_ARG, "fields must be 16-byte aligned");
+    if (out == cur) return fail(FD_ERR_INVALID_ARG, "out must not be cur (its neighbours' halos read it)");
+    const fd_desc &d = g->d;
+    const int R = d.r_xy;
+    const Launch &L = g->L;
+    IsoMaps maps;
+    if (cached_map(g, cur, L.tx + 2 * R, L.ty + 2 * R, &maps.cur) || cached_map(g, cur, L.tx, L.ty, &maps.cur_tile) ||
+        cached_map(g, prev, L.tx, L.ty, &maps.prev))
+        return fail(FD_ERR_CUDA, "tensor map encoding failed");
+    maps.kappa = g->tm_model[0];
+    IsoArgs a = iso_args(g);
+    a.prev = out;               // written: u^{n+1} (read through the map of prev)
+    a.cur = cur;
+    cudaError_t e = launch_iso(R, L, maps, a, g->stream);
+    if (e == cudaSuccess && g->nrec > 0 && !g->lattice)
+        e = launch_gather(out, g->lay.pitch, (long long)g->lay.pitch * d.ny, g->rec_idx, g->nrec, g->trace, g->rec_t0,
+                          g->rec_cap, g->st, g->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    g->n += 1;
+    return FD_OK;
+}
+
 int fd_set_graph(fd_grid_t *g, int steps)
 {
     if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");

@@ -34,7 +34,7 @@ FD_PTR_DEVICE = 1
 # every entry point declared in include/fd.h
 EXPORTS = [
     "fd_required_bytes", "fd_layout", "fd_stability_limit", "fd_create_grid", "fd_set_model",
-    "fd_add_source", "fd_add_source_series", "fd_set_receivers", "fd_step", "fd_run",
+    "fd_add_source", "fd_add_source_series", "fd_set_receivers", "fd_step", "fd_step_from", "fd_run",
     "fd_set_graph", "fd_read_receivers", "fd_get_state", "fd_set_state", "fd_field",
     "fd_set_launch", "fd_time_index", "fd_sync", "fd_destroy_grid", "fd_last_error",
     "fd_iso_step_static",
@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "fd_add_source_series": [_vp, _i, _i, _i, _vp, _i, _i],
             "fd_set_receivers": [_vp, _vp, _i, _vp, _i],
             "fd_step": [_vp],
+            "fd_step_from": [_vp, _vp, _vp, _vp],
             "fd_run": [_vp, _i],
             "fd_set_graph": [_vp, _i],
             "fd_read_receivers": [_vp, _i, _i, _vp, _i],
@@ -214,6 +215,10 @@ def fd_set_receivers(g, idx, nrec, trace_dev, nt_cap) -> None:
 
 def fd_step(g) -> None:
     _check(lib().fd_step(g))
+
+
+def fd_step_from(g, cur, prev, out) -> None:
+    _check(lib().fd_step_from(g, _ptr(cur), _ptr(prev), _ptr(out)))
 
 
 def fd_run(g, nsteps: int) -> None:

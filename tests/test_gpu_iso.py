@@ -357,3 +357,36 @@ def test_full_size_512_one_step_sampled(fd, O, R):
     assert np.abs(new[sel] - want).max() <= 2e-6 * scale
     # the receiver plane row of this step is the new level at k = 20
     np.testing.assert_array_equal(tr.reshape(512, 512), new[shot.nb])
+
+
+@pytest.mark.parametrize("R", [4, 8])
+def test_step_from_caller_levels_equals_fd_step(fd, R):
+    """fd_step_from: steps between caller-owned pitched levels (out of place,
+    and in place with out = prev) equal fd_step on the grid bit for bit, source
+    and receivers included; the grid's own levels are left alone."""
+    import torch
+    rec = synth.receiver_plane(50, 44, 9, stride=2)
+    shot = iso_shot(50, 44, 40, R, 12, seed=8, nb=5, src=(25, 22, 20), receivers=rec)
+    ref = fd.grid_from_shot(shot, device="cuda:0")
+    ref.run(4)
+    g = fd.grid_from_shot(shot, device="cuda:0")
+    g.run(4)
+    own = g.field_view(0).clone()
+    a, b = g.field_view(0).clone(), g.field_view(1).clone()
+    c = torch.empty_like(a)
+    fd.fd_step_from(g.h, a, b, c)      # u^5 into c
+    fd.fd_step_from(g.h, c, a, b)      # u^6 into b
+    fd.fd_step_from(g.h, b, c, c)      # u^7 in place over u^5
+    ref.run(3)
+    torch.cuda.synchronize()
+    nx = shot.nx
+    np.testing.assert_array_equal(c[:, :, :nx].cpu().numpy(), ref.field_view(0)[:, :, :nx].cpu().numpy())
+    np.testing.assert_array_equal(b[:, :, :nx].cpu().numpy(), ref.field_view(1)[:, :, :nx].cpu().numpy())
+    assert g.time_index == ref.time_index == 7
+    np.testing.assert_array_equal(g.traces(), ref.traces())
+    assert torch.equal(g.field_view(0), own)
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_step_from(g.h, a, b, a)
+    assert e.value.code == fd.FD_ERR_INVALID_ARG
+    g.close()
+    ref.close()

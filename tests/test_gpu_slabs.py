@@ -212,3 +212,28 @@ def test_rank_slabs_on_gloo_ranks_match_the_unsplit_grid(fd, mode, world):
         assert o[4] == shot.nsteps
     np.testing.assert_array_equal(tr, tr_ref)
     assert np.abs(tr_ref).max() > 0
+
+
+def test_step_parts_between_graph_runs(fd):
+    """Parts of a step interleave with graph-replayed runs of the same grid
+    (the graphs are kept per level parity): graph runs, a step in two parts,
+    graph runs again, an odd number of plain steps, equal fd_step throughout."""
+    rec = synth.receiver_plane(40, 36, 10, stride=3)
+    shot = iso_shot(40, 36, 44, 4, 30, seed=4, nb=5, src=(20, 18, 22), receivers=rec)
+    ref = fd.grid_from_shot(shot, device="cuda:0")
+    ref.run(shot.nsteps)
+    g = fd.grid_from_shot(shot, device="cuda:0")
+    g.set_graph(4)
+    g.run(8)
+    g.step_planes(0, 20, False)
+    g.step_planes(20, 44, True)
+    g.run(9)
+    g.step_planes(30, 44, False)
+    g.step_planes(0, 30, True)
+    g.run(11)
+    assert g.time_index == ref.time_index == shot.nsteps
+    for a, b in zip(g.state(), ref.state()):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(g.traces(), ref.traces())
+    g.close()
+    ref.close()
