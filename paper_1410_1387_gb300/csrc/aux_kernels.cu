@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include <cudaTypedefs.h>
 
@@ -15,7 +16,9 @@ namespace fdk {
 // that the library links no libcuda and loads on machines without a GPU.
 int encode_field_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, long long pitch, int bx, int by)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    // the driver's encoder, looked up once (atomically: host threads may encode at once)
+    static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> enc_cache{nullptr};
+    PFN_cuTensorMapEncodeTiled_v12000 enc = enc_cache.load(std::memory_order_acquire);
     if (!enc) {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -23,6 +26,7 @@ int encode_field_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, 
         if (e != cudaSuccess) return (int)e;
         if (q != cudaDriverEntryPointSuccess || !fn) return -1;
         enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        enc_cache.store(enc, std::memory_order_release);
     }
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * ny * 4};

@@ -23,9 +23,17 @@
 //   * the damping is applied in its deferred form G (2u - G u_prev + kappa Lu + s),
 //     which equals multiplying both new levels by G after each step (Cerjan)
 //     without rewriting u^n.
+//   * a consumer fences its plain reads of a slot (fence.proxy.async) before its
+//     warp releases the slot: the producer's next copy into it goes through the
+//     async proxy, which the release alone does not order after those reads;
+//   * consecutive single-shot steps are launched as programmatic dependents
+//     (register forms): a CTA sets up its barriers before it waits for the
+//     previous step, then takes its time index.
 // Compulsory HBM traffic: 16 bytes per point update (read u^n, u^{n-1}, kappa;
 // write u^{n+1}).  All waits are bounded (about 1 s); a CTA that gives up sets
 // an error flag, drains its copies in flight and exits.
+#include <atomic>
+
 #include "fd_internal.h"
 #include "launch_shape.h"
 #include "ptx.cuh"
@@ -678,14 +686,14 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
 {
     using C = IsoCfg<R, TX, TY, LA>;
     constexpr int smem_max = cmax(C::SMEM + 4 * kMaxChunk, C::SMEM_FLOOR);
-    static bool attr_set[64] = {};   // per device
+    static std::atomic<bool> attr_set[64];   // per device; host threads may launch at once
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(iso_sweep_kernel<R, TX, TY, LA, INJ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
     }
     IsoArgs a = a0;
     const int zn = a.nz - a.ztop - a.zb;   // planes of this launch
@@ -724,14 +732,14 @@ static cudaError_t launch_b(const int4 *items, int nitems, const BatchShot *shot
     using C = IsoCfg<R, TX, TY, LA>;
     constexpr int smem = cmax(C::SMEM + 4 * kMaxChunk + (int)sizeof(IsoArgs), C::SMEM_FLOOR);
     (void)max_zchunk;
-    static bool attr_set[64] = {};   // per device
+    static std::atomic<bool> attr_set[64];   // per device; host threads may launch at once
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(iso_batch_kernel<R, TX, TY, LA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
     }
     if (nitems <= 0) return cudaSuccess;
     iso_batch_kernel<R, TX, TY, LA><<<nitems, C::NT, smem, s>>>(items, shots);
@@ -756,14 +764,14 @@ static cudaError_t launch_g(const IsoMaps &tm, const CUtensorMap &tm_grad, const
 {
     using C = IsoCfg<R, TX, TY, LA, 3>;
     constexpr int smem_max = C::SMEM + 4 * kMaxChunk;
-    static bool attr_set[64] = {};   // per device
+    static std::atomic<bool> attr_set[64];   // per device; host threads may launch at once
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(iso_grad_kernel<R, TX, TY, LA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
     }
     IsoArgs a = a0;
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zchunk - 1) / a.zchunk);

@@ -3,21 +3,26 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "fd_internal.h"
 
 namespace fdk {
 
-// Streaming multiprocessors of the current device (cached per device; 152, a
-// GB300's count, if the query fails).
+// Streaming multiprocessors of the current device (cached per device, atomically:
+// host threads may ask at once; 152, a GB300's count, if the query fails).
 inline int device_sm_count()
 {
-    static int cache[64] = {};
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 152;
-    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    if (dev >= 0 && dev < 64) cache[dev] = n;
+    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 

@@ -18,6 +18,8 @@
 //     p (the smaller tile also cuts ring A's halo from 5.5x to 3.1x the tile).
 // Compulsory HBM traffic: 36 bytes per point update (read p, q, p_prev, q_prev,
 // kx, kn, kz; write p, q).
+#include <atomic>
+
 #include "fd_internal.h"
 #include "launch_shape.h"
 #include "ptx.cuh"
@@ -571,14 +573,14 @@ template <int RXY, int RZ, int TX, int TY, int LA>
 static cudaError_t launch_vt(const VtiMaps &tm, const VtiArgs &a0, cudaStream_t s)
 {
     using C = VtiCfg<RXY, RZ, TX, TY, LA>;
-    static bool attr_set[64] = {};
+    static std::atomic<bool> attr_set[64];   // per device; host threads may launch at once
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(vti_sweep_kernel<RXY, RZ, TX, TY, LA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
     }
     VtiArgs a = a0;
     const int zn = a.nz - a.ztop - a.zb;   // planes of this launch
