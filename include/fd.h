@@ -237,12 +237,15 @@ int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch);
  * depend on it).  tx x ty points per CTA (tx a multiple of 4), zchunk planes
  * per CTA, `lookahead` staged planes in flight.  A (tx, ty, lookahead)
  * combination that is not built into the library returns FD_ERR_UNSUPPORTED
- * and leaves the previous configuration in place; so does the radius-4
- * 32 x 16 tile, built but refused (in a batch it showed run-to-run last-bit
- * differences whose cause is not yet known).  A new grid starts with
- * 64 x 16, lookahead 3 (isotropic radius 4), 32 x 32, lookahead 2 (radius 8,
- * z queues in tensor memory) or 64 x 8, lookahead 2 (VTI), and a z chunk of
- * 32-96 planes fitted to whole waves of the CTAs the GPU holds at once.
+ * and leaves the previous configuration in place.  Built: isotropic radius 4:
+ * 64 x 16 (lookahead 2, 3, 4), 64 x 8, 128 x 8, 32 x 16 (lookahead 3);
+ * radius 8: 64 x 8 (lookahead 2, 3), 32 x 16, 32 x 32 (lookahead 2); VTI
+ * (12, 8): 64 x 8 (lookahead 2, 3), 32 x 16, 32 x 32 (lookahead 2).  A new
+ * grid starts with 64 x 16, lookahead 3 (isotropic radius 4), 32 x 32,
+ * lookahead 2 (radius 8, z queues in tensor memory; VTI at R_z = 8, q's z
+ * queues in tensor memory) or 64 x 8, lookahead 2 (other VTI radii), and a z
+ * chunk of 32-96 planes fitted to whole waves of the CTAs the GPU holds at
+ * once.
  */
 int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead);
 
