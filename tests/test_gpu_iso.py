@@ -390,3 +390,49 @@ def test_step_from_caller_levels_equals_fd_step(fd, R):
     assert e.value.code == fd.FD_ERR_INVALID_ARG
     g.close()
     ref.close()
+
+
+def test_host_threads_drive_grids_at_once(fd):
+    """Four host threads, each creating and running its own grid (radius 4 or
+    8, isotropic or VTI) on its own stream at the same time -- first calls,
+    launch-attribute and tensor-map caches included -- give the same traces and
+    levels bit for bit as the same shots run one after the other."""
+    import threading
+    import torch
+    shots = [iso_shot(40 + 8 * i, 36, 30, 4 if i % 2 == 0 else 8, 20, seed=50 + i, nb=4,
+                      receivers=synth.receiver_plane(40 + 8 * i, 36, 6, stride=2)) for i in range(3)]
+    v = synth.vti_shot(32, nsteps=20, seed=9, with_model=False)
+    v.v = synth.layered_model(32, 32, 32, 9)
+    v.eps, v.delta = synth.layered_anisotropy(32, 32, 32, 9)
+    shots.append(v)
+
+    def run(shot, stream):
+        with torch.cuda.stream(stream):
+            g = fd.grid_from_shot(shot, device="cuda:0")
+            g.run(shot.nsteps)
+            out = (g.state(), g.traces())
+            g.close()
+        return out
+
+    seq = [run(s, torch.cuda.current_stream()) for s in shots]
+    par = [None] * len(shots)
+    errs = []
+
+    def worker(i):
+        try:
+            torch.cuda.set_device(0)
+            par[i] = run(shots[i], torch.cuda.Stream())
+        except Exception as e:          # surfaced below
+            errs.append(e)
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(len(shots))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errs, errs
+    for (sa, ta), (sb, tb) in zip(seq, par):
+        for a, b in zip(sa, sb):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(ta, tb)
+        assert np.abs(ta).max() > 0
