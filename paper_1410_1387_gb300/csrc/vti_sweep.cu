@@ -623,7 +623,7 @@ Launch vti_default_launch(int rxy, int rz, int nx, int ny, int nz)
     (void)rxy;
     Launch L;
     // R_z = 8: 32 x 32 tiles, two rows per thread, q's z queues in tensor memory
-    // (512^3: 167.3 vs 159.2 Gpts/s for the one-row 64 x 8 form on one box)
+    // (512^3: +1.3 to +5.2 % against the one-row 64 x 8 form in same-box comparisons)
     L.tx = rz == 8 ? 32 : 64;
     L.ty = rz == 8 ? 32 : 8;
     L.lookahead = 2;
