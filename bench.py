@@ -50,8 +50,8 @@ WORKLOADS = {
     "vti512": dict(mode="vti", R=12, bytes_per_pt=36, kernel="vti_sweep_kernel"),
 }
 KERNEL_SRC = {"iso_sweep_kernel": "iso_sweep.cu", "vti_sweep_kernel": "vti_sweep.cu"}
-KERNEL_HEADERS = {"iso_sweep_kernel": ("tmem.cuh", "launch_shape.h"),   # besides ptx.cuh and fd_internal.h
-                  "vti_sweep_kernel": ("tmem.cuh", "launch_shape.h")}
+KERNEL_HEADERS = {"iso_sweep_kernel": ("tmem.cuh", "launch_shape.h", "rec_slot.cuh"),   # besides ptx.cuh and fd_internal.h
+                  "vti_sweep_kernel": ("tmem.cuh", "launch_shape.h", "rec_slot.cuh")}
 
 
 def parse():

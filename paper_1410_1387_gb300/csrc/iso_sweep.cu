@@ -37,6 +37,7 @@
 #include "fd_internal.h"
 #include "launch_shape.h"
 #include "ptx.cuh"
+#include "rec_slot.cuh"
 #include "tmem.cuh"
 
 namespace fdk {
@@ -134,8 +135,14 @@ __device__ __forceinline__ void update_row(const IsoArgs &a, float *prev, const 
         const float G = gu[e] * gyz;
         o[e] = fmaf(ku[e], acc[e], fmaf(2.f, cu[e], -G * pu[e]));
     }
-    if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len)
-        o[a.src.sx - gxi] += a.src.tab[n];
+    if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len) {
+        // constant indices only: an index computed at run time would put o in
+        // local memory, stored on every update
+        const float sv = a.src.tab[n];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (a.src.sx == gxi + e) o[e] += sv;
+    }
     if (INJ && k == a.inj.rk) {
         // lattice of additive sources (the adjoint's receiver residuals)
         const int ry = gyi - a.inj.ry0;
@@ -161,16 +168,8 @@ __device__ __forceinline__ void update_row(const IsoArgs &a, float *prev, const 
     }
 
     if (a.rec.on && k == a.rec.rk) {
-        const int ry = gyi - a.rec.ry0;
-        const int row = n - a.rec.t0;
-        if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 && row < a.rec.cap) {
-            float *trow = a.rec.trace + (long long)row * a.rec.nrec + (long long)(ry / a.rec.rsy) * a.rec.rnx;
-            for (int e = 0; e < 4; ++e) {
-                const int rx = gxi + e - a.rec.rx0;
-                if (gxi + e < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
-                    trow[rx / a.rec.rsx] = o[e];
-            }
-        }
+        const RecSlot rs = rec_slot(a.rec, gxi, gyi, a.nx);
+        if (rs.flags) rec_store(a.rec, rs, n, o);
     }
 }
 

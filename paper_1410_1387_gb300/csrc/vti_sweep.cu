@@ -23,6 +23,7 @@
 #include "fd_internal.h"
 #include "launch_shape.h"
 #include "ptx.cuh"
+#include "rec_slot.cuh"
 #include "tmem.cuh"
 
 namespace fdk {
@@ -99,9 +100,15 @@ __device__ __forceinline__ void vti_update_row(const VtiArgs &a, const int n, co
         oq[e] = fmaf(knu[e], hp[e], fmaf(2.f, qc[e], -G * qpu[e])) + zt;
     }
     if (k == a.src.sz && gyi == a.src.sy && a.src.sx >= gxi && a.src.sx < gxi + 4 && n < a.src.len) {
+        // constant indices only: an index computed at run time would put op and
+        // oq in local memory, stored on every update
         const float sv = a.src.tab[n];
-        op[a.src.sx - gxi] += sv;
-        if (a.src.into_q) oq[a.src.sx - gxi] += sv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (a.src.sx == gxi + e) {
+                op[e] += sv;
+                if (a.src.into_q) oq[e] += sv;
+            }
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -122,16 +129,8 @@ __device__ __forceinline__ void vti_update_row(const VtiArgs &a, const int n, co
             }
     }
     if (a.rec.on && k == a.rec.rk) {
-        const int ry = gyi - a.rec.ry0;
-        const int row = n - a.rec.t0;
-        if (ry >= 0 && ry % a.rec.rsy == 0 && ry / a.rec.rsy < a.rec.rny && row >= 0 && row < a.rec.cap) {
-            float *trow = a.rec.trace + (long long)row * a.rec.nrec + (long long)(ry / a.rec.rsy) * a.rec.rnx;
-            for (int e = 0; e < 4; ++e) {
-                const int rx = gxi + e - a.rec.rx0;
-                if (gxi + e < a.nx && rx >= 0 && rx % a.rec.rsx == 0 && rx / a.rec.rsx < a.rec.rnx)
-                    trow[rx / a.rec.rsx] = op[e];
-            }
-        }
+        const RecSlot rs = rec_slot(a.rec, gxi, gyi, a.nx);
+        if (rs.flags) rec_store(a.rec, rs, n, op);
     }
 }
 
