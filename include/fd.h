@@ -244,8 +244,8 @@ int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch);
  * grid starts with 64 x 16, lookahead 3 (isotropic radius 4), 32 x 32,
  * lookahead 2 (radius 8, z queues in tensor memory; VTI at R_z = 8, q's z
  * queues in tensor memory) or 64 x 8, lookahead 2 (other VTI radii), and a z
- * chunk of 32-96 planes fitted to whole waves of the CTAs the GPU holds at
- * once.
+ * chunk fitted to whole waves of the CTAs the GPU holds at once: 32-96 planes
+ * (isotropic), 32-64 (VTI).
  */
 int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead);
 

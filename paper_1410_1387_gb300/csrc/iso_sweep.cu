@@ -26,8 +26,8 @@
 //   * a consumer fences its plain reads of a slot (fence.proxy.async) before its
 //     warp releases the slot: the producer's next copy into it goes through the
 //     async proxy, which the release alone does not order after those reads;
-//   * consecutive single-shot steps are launched as programmatic dependents
-//     (register forms): a CTA sets up its barriers before it waits for the
+//   * consecutive single-shot steps are launched as programmatic dependents:
+//     a CTA sets up its barriers (and tensor memory) before it waits for the
 //     previous step, then takes its time index.
 // Compulsory HBM traffic: 16 bytes per point update (read u^n, u^{n-1}, kappa;
 // write u^{n+1}).  All waits are bounded (about 1 s); a CTA that gives up sets
@@ -702,10 +702,11 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
     const int smem = cmax(C::SMEM + 4 * ((a.zchunk + 3) / 4 * 4), C::SMEM_FLOOR);
     // Programmatic stream serialisation: consecutive steps overlap one CTA's
     // set-up with the previous step's last CTAs (each CTA waits for that step
-    // to complete before it reads anything the step writes).  Measured at
-    // 512^3: +0.7 % for the register-queue forms, -2.8 % for the radius-8
-    // tensor-memory form, which is therefore launched without it (its
-    // griddepcontrol instructions then return at once).
+    // to complete before it reads anything the step writes).  The tensor-memory
+    // form allocates its columns before that wait; shared memory keeps at most
+    // three of its CTAs on an SM, of either step, so 3 x 128 of the 512 columns
+    // always suffice.  Measured at 512^3: +0.7 % for radius 4, +0.8 % for the
+    // radius-8 tensor-memory form.
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = dim3(C::NT);
@@ -715,7 +716,7 @@ static cudaError_t launch_ti(const IsoMaps &tm, const IsoArgs &a0, cudaStream_t 
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = C::TQ ? 0 : 1;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, iso_sweep_kernel<R, TX, TY, LA, INJ>, tm.cur, tm.prev, tm.kappa, tm.cur_tile, a);
 }
 

@@ -29,15 +29,17 @@ inline int device_sm_count()
 // z chunk that fits the launch to the GPU: with `slots` CTAs resident at a time
 // and each CTA's time taken as (its planes + P), P the planes it loads before its
 // first output (2R), the step takes about waves x (zchunk + P).  Among the even
-// splits of nz into chunks of 32 to 96 planes, the cheapest (ties: the longer
+// splits of nz into chunks of 32 to `hi` planes, the cheapest (ties: the longer
 // chunk).  At 512^3 on 304 slots this picks 7 chunks of 74 planes (5.9 waves)
 // over 8 of 64 (6.7 waves, the last one three-quarters full).  Longer chunks
 // measured slower than the model says (fewer CTAs to overlap each one's start),
-// hence the 96-plane cap.
-inline int wave_zchunk(const Launch &L, int nx, int ny, int nz, long slots, int P)
+// hence the cap: 96 planes for the isotropic sweep, 64 for the VTI sweep, whose
+// 512^3 step measured fastest at 64 planes and slowest at 74 of 43-74.
+inline int wave_zchunk(const Launch &L, int nx, int ny, int nz, long slots, int P, int hi = 96)
 {
     const long tiles = (long)((nx + L.tx - 1) / L.tx) * ((ny + L.ty - 1) / L.ty);
-    const int lo = nz < 32 ? nz : 32, hi = 96;
+    const int lo = nz < 32 ? nz : 32;
+    if (hi < lo) hi = lo;
     if (slots < 1) slots = 1;
     int best = lo;
     long best_cost = -1;

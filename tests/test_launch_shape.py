@@ -1,8 +1,9 @@
 """Host logic of the default launch shape (no GPU): the wave-fitted z chunk of
 launch_shape.h, compiled with the host compiler against the CUDA headers.  It
 must end for every grid (an nz of 1 once made the search loop forever), stay
-within [min(32, nz), 96] and nz, and at 512^3 pick 7 chunks of 74 planes on
-152 SMs x 2 CTAs (radius 4) and x 3 CTAs (radius 8)."""
+within [min(32, nz), cap] and nz, and at 512^3 pick 7 chunks of 74 planes on
+152 SMs x 2 CTAs (radius 4) and x 3 CTAs (radius 8), and 8 of 64 for the VTI
+sweep (cap 64, 2 CTAs per SM)."""
 import os
 import shutil
 import subprocess
@@ -22,14 +23,16 @@ int main()
     for (int nz = 1; nz <= 3000; ++nz)
         for (int nx : xs)
             for (int ny : ys)
-                for (const fdk::Launch &L : shapes) {
-                    const int z = fdk::wave_zchunk(L, nx, ny, nz, 304, 8);
-                    const int lo = nz < 32 ? nz : 32;
-                    if (z < lo || z > nz || z > 96) ++bad;
-                }
-    printf("%ld %d %d %d %d\n", bad, fdk::wave_zchunk(shapes[0], 512, 512, 512, 304, 8),
+                for (const fdk::Launch &L : shapes)
+                    for (int hi : {96, 64}) {
+                        const int z = fdk::wave_zchunk(L, nx, ny, nz, 304, 8, hi);
+                        const int lo = nz < 32 ? nz : 32;
+                        if (z < lo || z > nz || z > hi) ++bad;
+                    }
+    printf("%ld %d %d %d %d %d\n", bad, fdk::wave_zchunk(shapes[0], 512, 512, 512, 304, 8),
            fdk::wave_zchunk(shapes[1], 512, 512, 512, 456, 16), fdk::wave_zchunk(shapes[0], 1, 1, 1, 304, 8),
-           fdk::wave_zchunk(shapes[0], 320, 320, 320, 304, 8));
+           fdk::wave_zchunk(shapes[0], 320, 320, 320, 304, 8),
+           fdk::wave_zchunk(shapes[1], 512, 512, 512, 304, 16, 64));
     return 0;
 }
 """
@@ -52,8 +55,9 @@ def test_wave_zchunk_ends_and_stays_in_bounds(tmp_path):
     assert b.returncode == 0, b.stderr[-2000:]
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0
-    bad, r4, r8, one, c320 = map(int, r.stdout.split())
+    bad, r4, r8, one, c320, vti = map(int, r.stdout.split())
     assert bad == 0
     assert r4 == 74 and r8 == 74          # 7 chunks: 1792 CTAs, 5.9 waves of 304 or 3.9 of 456
     assert one == 1
     assert c320 == 54                     # 6 chunks of 5 x 20 tiles: 600 CTAs, two waves of 304
+    assert vti == 64                      # 8 chunks: 2048 CTAs, 6.7 waves of 304
