@@ -432,14 +432,23 @@ def run_ours(args):
             g.set_launch(*[int(x) for x in args.launch.split(",")])
         if world > 1:
             dist.barrier()
+        # events on the grid's stream split the shot into its phases (device time)
+        ph = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         with torch.cuda.device(dev):
+            ph[0].record(g.stream)
             fd.fd_set_model(g.h, v_h.data_ptr(), eps_h.data_ptr() if eps_h is not None else None,
                             del_h.data_ptr() if del_h is not None else None, fd.FD_PTR_HOST)
+            ph[1].record(g.stream)
             fd.fd_run(g.h, nsh)
+            ph[2].record(g.stream)
             fd.fd_read_receivers(g.h, 0, nsh, tr_h.data_ptr(), fd.FD_PTR_HOST)
+            ph[3].record(g.stream)
         e2e_s = fdist.max_over_ranks(time.perf_counter() - t0, dev)
+        torch.cuda.synchronize(dev)
+        phases = {"model_up": ph[0].elapsed_time(ph[1]), "steps": ph[1].elapsed_time(ph[2]),
+                  "traces_down": ph[2].elapsed_time(ph[3])}
         g.close()
         del g
         torch.cuda.empty_cache()
@@ -447,7 +456,8 @@ def run_ours(args):
         e2e = {"value": pts * nsh * world / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": nmodel * pts * 4 / nsh,
                "d2h_bytes_per_step": len(shot.receivers) * 4,
-               "shot_seconds": e2e_s, "steps_per_shot": nsh}
+               "shot_seconds": e2e_s, "steps_per_shot": nsh,
+               "phases_ms": {k: round(v, 3) for k, v in phases.items()}}
 
     # ---- the other single-shot operators of the same size, device-timed --------------
     others = {}
