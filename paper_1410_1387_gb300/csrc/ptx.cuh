@@ -66,12 +66,30 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false when `limit` clock cycles pass without completion.
+// One probe with a suspend-time hint: a thread whose phase has not completed
+// may be suspended until it completes or about hint_ns nanoseconds pass, rather
+// than returning at once and spinning (which takes issue slots from the warps
+// doing the work).
+__device__ __forceinline__ bool mbar_test_suspend(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false when `limit` clock cycles pass without completion.  Each
+// probe after the first may sleep up to 1 ms, far below the limit.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit)
 {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_test(bar, parity)) {
+    while (!mbar_test_suspend(bar, parity, 1000000u)) {
         if (clock64() - t0 > limit) return false;
     }
     return true;
