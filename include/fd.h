@@ -213,6 +213,23 @@ int fd_set_graph(fd_grid_t *g, int steps);
 int fd_read_receivers(fd_grid_t *g, int t_begin, int t_count, float *dst, int dst_kind);
 
 /*
+ * nsteps time steps, as fd_run, with their receiver rows streamed to the host
+ * while later steps compute: host_dst receives nsteps * nrec floats, row m
+ * holding step n_call + m (n_call = the time index at this call; receiver
+ * order as in fd_set_receivers).  The steps run in chunks of chunk_steps
+ * (0 = 64; at least nsteps / 256; rounded up to whole graphs when fd_set_graph
+ * is on); each chunk's rows are copied on a stream of the grid's own once the
+ * chunk's steps are done.  host_dst belongs to the caller and should be pinned
+ * (cudaHostAlloc or registered) for the copies to run asynchronously; pageable
+ * memory works, its copies staged by the host.  Returns after the last row has
+ * arrived and the device status has been read (FD_ERR_TIMEOUT as fd_sync).
+ * FD_ERR_BAD_STATE without receivers or a model; FD_ERR_OUT_OF_RANGE if the
+ * receiver buffer cannot hold the steps (nothing is enqueued then).  The paper
+ * records no receivers; this is the host side of the fused receiver lattice.
+ */
+int fd_run_to_host(fd_grid_t *g, int nsteps, float *host_dst, int chunk_steps);
+
+/*
  * Copy the stored state out as dense nz x ny x nx arrays (any pointer may be
  * NULL).  cur = u^n (VTI: p^n), prev = the stored older level, q_cur / q_prev
  * the same for q (VTI).  The older level is stored before its second damping

@@ -149,6 +149,9 @@ struct fd_grid {
     int graph_steps = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // fd_run_to_host: trace rows go to the host on their own stream, one event per chunk of steps
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_ev;
 };
 
 namespace {
@@ -888,6 +891,48 @@ int fd_run(fd_grid_t *g, int nsteps)
     return FD_OK;
 }
 
+int fd_run_to_host(fd_grid_t *g, int nsteps, float *host_dst, int chunk_steps)
+{
+    int rc = check_ready(g, nsteps);
+    if (rc) return rc;
+    if (g->nrec == 0) return fail(FD_ERR_BAD_STATE, "no receivers");
+    if (chunk_steps < 0 || (nsteps > 0 && !host_dst)) return fail(FD_ERR_INVALID_ARG, "bad arguments");
+    if (nsteps == 0) return FD_OK;
+    // chunks: 64 steps unless asked otherwise, whole graphs when graphs are on,
+    // at most 256 of them (one event each)
+    int c = chunk_steps > 0 ? chunk_steps : 64;
+    c = std::max(c, (nsteps + 255) / 256);
+    if (g->graph_steps > 0) c = (c + g->graph_steps - 1) / g->graph_steps * g->graph_steps;
+    const int nchunks = (nsteps + c - 1) / c;
+    if (!g->copy_stream) CU(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking), "stream create");
+    while ((int)g->copy_ev.size() < nchunks) {
+        cudaEvent_t e = nullptr;
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event create");
+        g->copy_ev.push_back(e);
+    }
+    // every chunk's steps first (a pageable destination then still overlaps:
+    // its staged copies run on the host while later chunks compute) ...
+    const long long row0 = (long long)g->n - g->rec_t0;
+    for (int i = 0; i < nchunks; ++i) {
+        rc = fd_run(g, std::min(c, nsteps - i * c));
+        if (rc) {
+            cudaStreamSynchronize(g->stream);
+            return rc;
+        }
+        CU(cudaEventRecord(g->copy_ev[i], g->stream), "event record");
+    }
+    // ... then each chunk's rows once its steps are done
+    for (int i = 0; i < nchunks; ++i) {
+        const int ci = std::min(c, nsteps - i * c);
+        CU(cudaStreamWaitEvent(g->copy_stream, g->copy_ev[i], 0), "stream wait");
+        CU(cudaMemcpyAsync(host_dst + (size_t)i * c * g->nrec, g->trace + (size_t)(row0 + (long long)i * c) * g->nrec,
+                           (size_t)ci * g->nrec * sizeof(float), cudaMemcpyDeviceToHost, g->copy_stream),
+           "trace copy");
+    }
+    CU(cudaStreamSynchronize(g->copy_stream), "copy stream synchronize");
+    return check_dev_status(g);
+}
+
 int fd_read_receivers(fd_grid_t *g, int t_begin, int t_count, float *dst, int dst_kind)
 {
     if (!g) return fail(FD_ERR_INVALID_ARG, "grid is NULL");
@@ -1078,6 +1123,11 @@ int fd_destroy_grid(fd_grid_t *g)
     if (!g) return FD_OK;
     drop_graphs(g);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->copy_stream) {
+        cudaStreamSynchronize(g->copy_stream);
+        cudaStreamDestroy(g->copy_stream);
+    }
+    for (cudaEvent_t e : g->copy_ev) cudaEventDestroy(e);
     // stream-ordered frees: after this grid's enqueued work, without a device-wide sync
     void *bufs[] = {g->st, g->gx, g->gy, g->gz, g->ztab, g->src_tab, g->rec_idx, g->d_misfit};
     for (void *p : bufs)

@@ -35,7 +35,7 @@ FD_PTR_DEVICE = 1
 EXPORTS = [
     "fd_required_bytes", "fd_layout", "fd_stability_limit", "fd_create_grid", "fd_set_model",
     "fd_add_source", "fd_add_source_series", "fd_set_receivers", "fd_step", "fd_step_from", "fd_run",
-    "fd_set_graph", "fd_read_receivers", "fd_get_state", "fd_set_state", "fd_field",
+    "fd_set_graph", "fd_read_receivers", "fd_run_to_host", "fd_get_state", "fd_set_state", "fd_field",
     "fd_set_launch", "fd_time_index", "fd_sync", "fd_destroy_grid", "fd_last_error",
     "fd_iso_step_static",
     "fd_batch_create", "fd_batch_set_launch", "fd_batch_set_graph", "fd_batch_add", "fd_batch_remove",
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
             "fd_run": [_vp, _i],
             "fd_set_graph": [_vp, _i],
             "fd_read_receivers": [_vp, _i, _i, _vp, _i],
+            "fd_run_to_host": [_vp, _i, _vp, _i],
             "fd_get_state": [_vp, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_i)],
             "fd_set_state": [_vp, _vp, _vp, _vp, _vp, _i, _i],
             "fd_field": [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)],
@@ -235,6 +236,10 @@ def fd_set_launch(g, tx, ty, zchunk, lookahead) -> None:
 
 def fd_read_receivers(g, t_begin, t_count, dst, dst_kind) -> None:
     _check(lib().fd_read_receivers(g, t_begin, t_count, _ptr(dst), dst_kind))
+
+
+def fd_run_to_host(g, nsteps, host_dst, chunk_steps=0) -> None:
+    _check(lib().fd_run_to_host(g, nsteps, _ptr(host_dst), chunk_steps))
 
 
 def fd_get_state(g, cur=None, prev=None, q_cur=None, q_prev=None, ptr_kind=FD_PTR_HOST) -> int:
@@ -463,6 +468,17 @@ class Grid:
     @property
     def time_index(self) -> int:
         return fd_time_index(self.h)
+
+    def run_to_host(self, nsteps: int, out=None, chunk_steps: int = 0):
+        """nsteps steps with their receiver rows streamed to host memory while
+        later steps compute (fd_run_to_host); returns the (nsteps, nrec) rows
+        (`out` if given: pinned memory lets the copies run asynchronously)."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty((nsteps, max(self.nrec, 1)), dtype=torch.float32).pin_memory()
+        with torch.cuda.device(self.device):
+            fd_run_to_host(self.h, nsteps, out, chunk_steps)
+        return out
 
     # read back --------------------------------------------------------------------
     def traces(self, t_begin=0, t_count=None) -> np.ndarray:

@@ -436,3 +436,48 @@ def test_host_threads_drive_grids_at_once(fd):
             np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(ta, tb)
         assert np.abs(ta).max() > 0
+
+
+@pytest.mark.parametrize("mode,graph,chunk", [("iso", 0, 0), ("iso", 0, 7), ("iso", 4, 5), ("vti", 0, 6)])
+def test_run_to_host_streams_the_traces(fd, mode, graph, chunk):
+    """fd_run_to_host: the receiver rows it streams to the host while later steps
+    compute -- into pinned and into pageable memory, with chunks that do not
+    divide the step count, with graphs on -- equal fd_run followed by
+    fd_read_receivers bit for bit; a run the trace buffer cannot hold, or one
+    without receivers, is refused with nothing enqueued."""
+    import torch
+    if mode == "iso":
+        rec = synth.receiver_plane(52, 40, 7)          # full-rate lattice: 16-byte stores
+        shot = iso_shot(52, 40, 36, 4, 60, seed=9, nb=5, src=(26, 20, 18), receivers=rec)
+    else:
+        shot = synth.vti_shot(40, nsteps=60, seed=4)
+        rec = shot.receivers
+    ref = fd.grid_from_shot(shot, device="cuda:0", nt_cap=60)
+    ref.run(56)
+    want = ref.traces()
+    g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=60)
+    if graph:
+        g.set_graph(graph)
+    g.run(3)
+    pinned = torch.empty((33, len(rec)), dtype=torch.float32).pin_memory()
+    g.run_to_host(33, pinned, chunk)
+    assert g.time_index == 36
+    page = np.empty((20, len(rec)), np.float32)
+    fd.fd_run_to_host(g.h, 20, page, chunk)
+    assert g.time_index == 56
+    np.testing.assert_array_equal(pinned.numpy(), want[3:36])
+    np.testing.assert_array_equal(page, want[36:56])
+    np.testing.assert_array_equal(g.traces(), want)
+    fd.fd_run_to_host(g.h, 0, None, chunk)             # nothing to do
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_run_to_host(g.h, 5, page, chunk)          # rows 56..60: the buffer holds 60
+    assert e.value.code == fd.FD_ERR_OUT_OF_RANGE
+    assert g.time_index == 56
+    g.close()
+    ref.close()
+    bare = fd.grid_from_shot(shot, device="cuda:0", receivers=False)
+    with pytest.raises(fd.FdError) as e:
+        fd.fd_run_to_host(bare.h, 2, page, 0)
+    assert e.value.code == fd.FD_ERR_BAD_STATE
+    assert bare.time_index == 0
+    bare.close()
