@@ -3,8 +3,9 @@
  * the CUDA runtime; no Python): the caller allocates the arena and the trace
  * buffer, sets a model with a vertical velocity gradient v = 1800 + 10 k m/s,
  * a Ricker source at the centre, an x line of receivers through the centre,
- * runs `steps` steps as CUDA graphs of 8 steps, and writes the traces
- * (steps x n floats) and then u^n (n^3 floats) to `out`.
+ * runs `steps` steps as CUDA graphs of 8 steps (the second half through
+ * fd_run_to_host, whose streamed rows must equal the ones read back after), and
+ * writes the traces (steps x n floats) and then u^n (n^3 floats) to `out`.
  *
  * usage: shot_abi n radius steps sponge_width dt out
  */
@@ -77,11 +78,22 @@ int main(int argc, char **argv)
     check_cuda(cudaMalloc((void **)&trace_dev, sizeof(float) * (size_t)steps * n), "traces");
     check(fd_set_receivers(g, idx, n, trace_dev, steps), "fd_set_receivers");
     check(fd_set_graph(g, 8), "fd_set_graph");
-    check(fd_run(g, steps), "fd_run");
+    /* the first half by fd_run, the rest with its rows streamed to pinned host memory */
+    const int half = steps / 2;
+    check(fd_run(g, half), "fd_run");
+    float *streamed = NULL;
+    check_cuda(cudaMallocHost((void **)&streamed, sizeof(float) * (size_t)(steps - half) * n), "pinned rows");
+    check(fd_run_to_host(g, steps - half, streamed, 0), "fd_run_to_host");
 
     float *tr = (float *)malloc(sizeof(float) * (size_t)steps * n);
     float *u = (float *)malloc(sizeof(float) * (size_t)n * n * n);
     check(fd_read_receivers(g, 0, steps, tr, FD_PTR_HOST), "fd_read_receivers");
+    for (size_t i = 0; i < (size_t)(steps - half) * n; ++i)
+        if (streamed[i] != tr[(size_t)half * n + i]) {
+            fprintf(stderr, "streamed row value %zu differs from the read-back one\n", i);
+            return 1;
+        }
+    check_cuda(cudaFreeHost(streamed), "free pinned rows");
     int tn = -1;
     check(fd_get_state(g, u, NULL, NULL, NULL, FD_PTR_HOST, &tn), "fd_get_state");
     if (tn != steps) {

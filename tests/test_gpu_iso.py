@@ -481,3 +481,35 @@ def test_run_to_host_streams_the_traces(fd, mode, graph, chunk):
     assert e.value.code == fd.FD_ERR_BAD_STATE
     assert bare.time_index == 0
     bare.close()
+
+
+@pytest.mark.parametrize("mode,R,launch", [("iso", 4, None), ("iso", 8, None), ("iso", 8, (64, 8, 17, 3)),
+                                           ("vti", 12, None), ("vti", 12, (64, 8, 17, 2))])
+@pytest.mark.parametrize("lat", [dict(stride=1), dict(stride=1, x0=1, nrx=37), dict(stride=1, x0=4, nrx=6, nry=3),
+                                 dict(stride=2, x0=3, y0=1), dict(stride=3, x0=2, y0=2),
+                                 dict(stride=5, x0=4, y0=7, nrx=1, nry=1)])
+def test_lattice_receivers_record_the_new_level(fd, mode, R, launch, lat):
+    """The fused receiver lattice -- 16-byte stores where a thread's 4 points are
+    4 aligned receivers, single stores otherwise (offset and ragged lattices,
+    strides 2, 3, 5, one receiver) -- records after every step exactly the new
+    level (p for VTI) at its points, in lattice order, in the two-row and the
+    one-row forms."""
+    import torch
+    n = 40
+    rec = synth.receiver_plane(n + (13 if mode == "iso" else 0), n - 2 if mode == "iso" else n, 9, **lat)
+    if mode == "iso":
+        shot = iso_shot(n + 13, n - 2, 30, R, 6, seed=3, nb=4, src=(8, 4, 10), receivers=rec)
+    else:
+        shot = synth.vti_shot(n, nsteps=6, seed=3)
+        shot.src = (8, 4, 10)      # within three steps of every lattice's points
+        shot.receivers = rec
+    g = fd.grid_from_shot(shot, device="cuda:0", nt_cap=6)
+    if launch:
+        g.set_launch(*launch)
+    for t in range(6):
+        g.step()
+        torch.cuda.synchronize()
+        f = g.field_view(0)[:, :, :shot.nx].cpu().numpy()
+        np.testing.assert_array_equal(g.traces(t, 1)[0], f[rec[:, 2], rec[:, 1], rec[:, 0]])
+    assert np.count_nonzero(g.traces()) > 0
+    g.close()
