@@ -222,7 +222,9 @@ int fd_read_receivers(fd_grid_t *g, int t_begin, int t_count, float *dst, int ds
  * chunk's steps are done.  host_dst belongs to the caller and should be pinned
  * (cudaHostAlloc or registered) for the copies to run asynchronously; pageable
  * memory works, its copies staged by the host.  Returns after the last row has
- * arrived and the device status has been read (FD_ERR_TIMEOUT as fd_sync).
+ * arrived and the device status has been read (FD_ERR_TIMEOUT as fd_sync);
+ * it synchronises, so it is not to be called while the grid's stream is being
+ * captured into a graph.
  * FD_ERR_BAD_STATE without receivers or a model; FD_ERR_OUT_OF_RANGE if the
  * receiver buffer cannot hold the steps (nothing is enqueued then).  The paper
  * records no receivers; this is the host side of the fused receiver lattice.
