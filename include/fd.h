@@ -257,14 +257,14 @@ int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch);
  * per CTA, `lookahead` staged planes in flight.  A (tx, ty, lookahead)
  * combination that is not built into the library returns FD_ERR_UNSUPPORTED
  * and leaves the previous configuration in place.  Built: isotropic radius 4:
- * 64 x 16 (lookahead 2, 3, 4), 64 x 8, 128 x 8, 32 x 16 (lookahead 3);
- * radius 8: 64 x 8 (lookahead 2, 3), 32 x 16, 32 x 32 (lookahead 2); VTI
- * (12, 8): 64 x 8 (lookahead 2, 3), 32 x 16, 32 x 32 (lookahead 2).  A new
- * grid starts with 64 x 16, lookahead 3 (isotropic radius 4), 32 x 32,
- * lookahead 2 (radius 8, z queues in tensor memory; VTI at R_z = 8, q's z
- * queues in tensor memory) or 64 x 8, lookahead 2 (other VTI radii), and a z
- * chunk fitted to whole waves of the CTAs the GPU holds at once: 32-96 planes
- * (isotropic), 32-64 (VTI).
+ * 64 x 16 (lookahead 2, 3, 4), 64 x 8, 128 x 8, 32 x 16 (lookahead 3),
+ * 32 x 32 (lookahead 2, 3); radius 8: 64 x 8 (lookahead 2, 3), 32 x 16,
+ * 32 x 32 (lookahead 2); VTI (12, 8): 64 x 8 (lookahead 2, 3), 32 x 16,
+ * 32 x 32 (lookahead 2).  32 x 32 tiles keep the z queues in tensor memory.
+ * A new grid starts with 32 x 32, lookahead 3 (isotropic radius 4), 32 x 32,
+ * lookahead 2 (radius 8; VTI at R_z = 8) or 64 x 8, lookahead 2 (other VTI
+ * radii), and a z chunk fitted to whole waves of the CTAs the GPU holds at
+ * once: 32-96 planes (isotropic), 32-64 (VTI).
  */
 int fd_set_launch(fd_grid_t *g, int tx, int ty, int zchunk, int lookahead);
 

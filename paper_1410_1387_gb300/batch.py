@@ -133,7 +133,7 @@ def run_per_shot(shots, device=None, keep_grids=False):
 # --------------------------------------------------------------------------
 
 # candidate (tx, ty, lookahead) per radius; every one is built into libfd.so
-TILES = {4: [(64, 16, 3), (64, 16, 2), (64, 16, 4), (128, 8, 3), (64, 8, 3), (32, 16, 3)],
+TILES = {4: [(64, 16, 3), (64, 16, 2), (64, 16, 4), (128, 8, 3), (64, 8, 3), (32, 16, 3), (32, 32, 3), (32, 32, 2)],
          8: [(32, 32, 2), (64, 8, 2), (64, 8, 3), (32, 16, 2)]}
 ZCHUNKS = [16, 32, 64, 96, 128]
 

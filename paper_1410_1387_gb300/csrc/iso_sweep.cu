@@ -16,9 +16,9 @@
 //   * each consumer thread owns 4 consecutive x points (one float4) of one row
 //     and keeps their 2R+1 z neighbours in registers (plane k + R enters from
 //     ring B); x and y neighbours come from the staged plane (x as 1 + R/2
-//     aligned float4 reads, y as 2R).  Radius 8 in 32 x 32 tiles keeps the z
-//     neighbours in tensor memory instead, and each thread takes two adjacent
-//     rows, which share their y reads;
+//     aligned float4 reads, y as 2R).  32 x 32 tiles (the default at radius 4
+//     and 8) keep the z neighbours in tensor memory instead, and each thread
+//     takes two adjacent rows, which share their y reads;
 //   * u^{n+1} is written in place over u^{n-1} with 128-bit evict-first stores
 //     (each point's older value was staged before any thread writes it);
 //   * the damping is applied in its deferred form G (2u - G u_prev + kappa Lu + s),
@@ -51,10 +51,13 @@ constexpr long long kWaitLimit = 2000000000LL;
 template <int R, int TX, int TY, int LA, int NBT = 2>
 struct IsoCfg {
     static constexpr int NTX = TX / 4;              // consumer threads per tile row
-    // Radius 8 in 32 x 32 tiles (the forward and adjoint sweeps; not the gradient
-    // sweep) keeps its z queues in tensor memory, which frees the registers for
-    // two tile rows per thread: the rows share their y-neighbour reads.
-    static constexpr bool TQ = (R == 8 && TX == 32 && TY == 32 && NBT == 2);
+    // 32 x 32 tiles (radius 4 and 8; the forward and adjoint sweeps, not the
+    // gradient sweep) keep their z queues in tensor memory, which frees the
+    // registers for two tile rows per thread: the rows share their y-neighbour
+    // reads.
+    static constexpr bool TQ = ((R == 8 || R == 4) && TX == 32 && TY == 32 && NBT == 2);
+    static constexpr int QS = 2 * R;                // queue ring slots per row
+    static constexpr int QC = 4 * QS;               // tensor-memory columns per row
     static constexpr int RPT = TQ ? 2 : 1;          // tile rows per consumer thread
     static constexpr int NC = NTX * TY / RPT;       // consumer threads
     static constexpr int NCW = NC / 32;             // consumer warps
@@ -70,11 +73,13 @@ struct IsoCfg {
     static constexpr int SLOT_B = NBT_ALL * TX * TY;   // floats per ring B plane
     static constexpr int NA = LA + 1;               // ring A slots
     // CTAs per SM the registers are budgeted for
-    static constexpr int MINB = TQ ? 3 : (NT <= 160 ? (R >= 8 ? 3 : 4) : 2);
-    // Tensor memory per CTA: two rows x 64 columns.  Shared memory (over 57 KB a
-    // CTA) keeps at most three such CTAs on an SM, so their allocations (3 x 128
-    // of the 512 columns) never wait.
-    static constexpr int TMEM_COLS = 128;
+    static constexpr int MINB = TQ ? ((R == 4 && LA == 2) ? 4 : 3) : (NT <= 160 ? (R >= 8 ? 3 : 4) : 2);
+    // Tensor memory per CTA: two rows x 4 QS columns (radius 8: 128, radius 4:
+    // 64).  Shared memory keeps at most three radius-8 CTAs (65 KB each) or four
+    // radius-4 ones (55 KB at lookahead 2, 74 KB at 3) on an SM, so their
+    // allocations (at most 384 of the 512 columns; any mix with the VTI sweep's
+    // 128-column CTAs of 112 KB stays below 450) never wait.
+    static constexpr int TMEM_COLS = 2 * QC;
     static constexpr int SMEM_FLOOR = 0;
     static constexpr int NB = LA + 1;               // ring B slots
     static constexpr int OFF_B = NA * SLOT_A * 4;
@@ -347,7 +352,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 __syncwarp();
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
-                    tmem_st4(tl + 64 * e + 4 * (uint32_t)((vk0 - R + m0 + m) & 15), v[m]);
+                    tmem_st4(tl + C::QC * e + 4 * (uint32_t)((vk0 - R + m0 + m) & (C::QS - 1)), v[m]);
                 }
             }
         }
@@ -456,7 +461,7 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 // from their slots (vk + 8 is the entering one; its slot still holds
                 // vk - 8)
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
+                for (int h = 0; h < R / 4; ++h)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         uint32_t c[8];
@@ -464,20 +469,20 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int l = 4 * h + 1 + i;
-                            c[2 * i] = tl + 64 * e + 4 * (uint32_t)((vk + l) & 15);
-                            c[2 * i + 1] = tl + 64 * e + 4 * (uint32_t)((vk - l) & 15);
+                            c[2 * i] = tl + C::QC * e + 4 * (uint32_t)((vk + l) & (C::QS - 1));
+                            c[2 * i + 1] = tl + C::QC * e + 4 * (uint32_t)((vk - l) & (C::QS - 1));
                         }
                         __syncwarp();
                         tmem_ld4x8(c, v);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             const int l = 4 * h + 1 + i;
-                            pair(e, a.wz2[l], l == 8 ? qin[e] : v[2 * i], v[2 * i + 1]);
+                            pair(e, a.wz2[l], l == R ? qin[e] : v[2 * i], v[2 * i + 1]);
                         }
                     }
                 // vk + 8 takes the slot of vk - 8, no longer needed
-                const uint32_t cs = tl + 4 * (uint32_t)((vk + R) & 15);
-                tmem_st4_2(cs, qin[0], cs + 64, qin[1]);
+                const uint32_t cs = tl + 4 * (uint32_t)((vk + R) & (C::QS - 1));
+                tmem_st4_2(cs, qin[0], cs + C::QC, qin[1]);
             }
 
 #pragma unroll
@@ -791,12 +796,14 @@ static cudaError_t launch_g(const IsoMaps &tm, const CUtensorMap &tm_grad, const
 
 Launch iso_grad_launch(int R, int nx, int ny, int nz)
 {
-    Launch L = iso_default_launch(R, nx, ny, nz);
-    if (R == 8) {
-        // the gradient sweep keeps the register queue: three CTAs of 32 x 16 per SM
-        L.ty = 16;
-        L.zchunk = default_zchunk(L, nx, ny, nz, 4096);
-    }
+    // the gradient sweep keeps the register queue: radius 4 in 64 x 16 tiles (two
+    // CTAs per SM), radius 8 in 32 x 16 (three)
+    Launch L;
+    L.tx = R == 8 ? 32 : 64;
+    L.ty = 16;
+    L.lookahead = R == 8 ? 2 : 3;
+    L.zchunk = R == 8 ? default_zchunk(L, nx, ny, nz, 4096)
+                      : wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<4, 64, 16, 3>::MINB, 2 * R);
     return L;
 }
 
@@ -816,6 +823,8 @@ cudaError_t launch_iso_grad(int R, const Launch &L, const IsoMaps &tm, const CUt
     X(4, 64, 8, 3)        \
     X(4, 128, 8, 3)       \
     X(4, 32, 16, 3)       \
+    X(4, 32, 32, 2)       \
+    X(4, 32, 32, 3)       \
     X(8, 64, 8, 2)        \
     X(8, 64, 8, 3)        \
     X(8, 32, 16, 2)       \
@@ -854,10 +863,13 @@ Launch iso_default_launch(int R, int nx, int ny, int nz)
 {
     Launch L;
     if (R == 4) {
-        L.tx = 64;
-        L.ty = 16;
+        // three CTAs of 32 x 32 per SM, z queues in tensor memory, two rows per
+        // thread (512^3: 401.7 vs 394.6 Gpts/s for the one-row 64 x 16 form,
+        // interleaved in one process)
+        L.tx = 32;
+        L.ty = 32;
         L.lookahead = 3;
-        L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<4, 64, 16, 3>::MINB, 2 * R);
+        L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<4, 32, 32, 3>::MINB, 2 * R);
     } else {
         // two CTAs of 32 x 32 per SM (z queues in tensor memory, two rows per thread)
         L.tx = 32;

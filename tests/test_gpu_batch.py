@@ -140,7 +140,7 @@ def test_autotuner_caches_a_built_choice(fdm, tmp_path):
 # for every radius-4 tile built into the library, twice each: traces bit for bit
 # equal to the per-shot loop's.  Traces stay on the device (10.6 GB per pass).
 
-R4_TILES = [(64, 16, 3), (64, 16, 2), (64, 16, 4), (128, 8, 3), (64, 8, 3), (32, 16, 3)]
+R4_TILES = [(64, 16, 3), (64, 16, 2), (64, 16, 4), (128, 8, 3), (64, 8, 3), (32, 16, 3), (32, 32, 3), (32, 32, 2)]
 
 
 @pytest.fixture(scope="module")

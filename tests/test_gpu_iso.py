@@ -129,16 +129,21 @@ def test_grid_beyond_2_to_the_31_points(fd):
 
 
 def test_axis_beyond_the_launch_grid_is_refused(fd):
-    """2^20 points along y (the largest axis a description may have) need more
-    than 65535 tiles of 16 rows: creation reports it instead of launching."""
+    """2^20 points along y (the largest axis a description may have) fit the
+    default 32-row tiles (32768 of them) but need more than 65535 tiles of 16
+    rows: that launch shape is refused instead of launched, and the grid keeps
+    its own."""
     import torch
     d, _ = fd.make_desc(fd.FD_MODE_ISO, 1, 1 << 20, 1, 4, 4, 10.0, 10.0, 1e-4)
     nbytes = fd.fd_required_bytes(d)
     arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda:0")
     ptr = arena.data_ptr() + (-arena.data_ptr()) % 256
+    h = fd.fd_create_grid(d, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
     with pytest.raises(fd.FdError) as e:
-        fd.fd_create_grid(d, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
+        fd.fd_set_launch(h, 64, 16, 64, 3)
     assert e.value.code == fd.FD_ERR_INVALID_ARG
+    fd.fd_set_launch(h, 32, 32, 64, 3)
+    fd.fd_destroy_grid(h)
     d2, _ = fd.make_desc(fd.FD_MODE_ISO, 1, 1, (1 << 20) + 1, 4, 4, 10.0, 10.0, 1e-4)
     with pytest.raises(fd.FdError) as e:
         fd.fd_required_bytes(d2)
@@ -176,9 +181,12 @@ def test_graph_and_tiles_are_bitwise_identical(fd):
     (u1, p1), t1 = _run_gpu(fd, shot, 24, set_graph=(8,))
     (u2, p2), t2 = _run_gpu(fd, shot, 24, set_launch=(64, 8, 13, 3))
     (u3, p3), t3 = _run_gpu(fd, shot, 24, set_launch=(128, 8, 60, 3))
-    for a, b in ((u0, u1), (u0, u2), (u0, u3), (p0, p1), (p0, p3)):
+    (u4, p4), t4 = _run_gpu(fd, shot, 24, set_launch=(64, 16, 13, 3))
+    (u5, p5), t5 = _run_gpu(fd, shot, 24, set_launch=(32, 32, 13, 2))
+    for a, b in ((u0, u1), (u0, u2), (u0, u3), (u0, u4), (u0, u5), (p0, p1), (p0, p3), (p0, p4), (p0, p5)):
         np.testing.assert_array_equal(a, b)
-    np.testing.assert_array_equal(t0, t2)
+    for t in (t2, t4, t5):
+        np.testing.assert_array_equal(t0, t)
 
 
 @pytest.mark.parametrize("launch", [(64, 8, 17, 3), (32, 16, 9, 2), (32, 32, 9, 2)])
@@ -483,7 +491,8 @@ def test_run_to_host_streams_the_traces(fd, mode, graph, chunk):
     bare.close()
 
 
-@pytest.mark.parametrize("mode,R,launch", [("iso", 4, None), ("iso", 8, None), ("iso", 8, (64, 8, 17, 3)),
+@pytest.mark.parametrize("mode,R,launch", [("iso", 4, None), ("iso", 4, (64, 16, 17, 3)), ("iso", 8, None),
+                                           ("iso", 8, (64, 8, 17, 3)),
                                            ("vti", 12, None), ("vti", 12, (64, 8, 17, 2))])
 @pytest.mark.parametrize("lat", [dict(stride=1), dict(stride=1, x0=1, nrx=37), dict(stride=1, x0=4, nrx=6, nry=3),
                                  dict(stride=2, x0=3, y0=1), dict(stride=3, x0=2, y0=2),
@@ -492,8 +501,8 @@ def test_lattice_receivers_record_the_new_level(fd, mode, R, launch, lat):
     """The fused receiver lattice -- 16-byte stores where a thread's 4 points are
     4 aligned receivers, single stores otherwise (offset and ragged lattices,
     strides 2, 3, 5, one receiver) -- records after every step exactly the new
-    level (p for VTI) at its points, in lattice order, in the two-row and the
-    one-row forms."""
+    level (p for VTI) at its points, in lattice order, in the two-row forms (the
+    defaults) and the one-row forms."""
     import torch
     n = 40
     rec = synth.receiver_plane(n + (13 if mode == "iso" else 0), n - 2 if mode == "iso" else n, 9, **lat)
