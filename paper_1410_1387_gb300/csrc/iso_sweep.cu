@@ -179,6 +179,22 @@ __device__ __forceinline__ void update_row(const IsoArgs &a, float *prev, const 
     }
 }
 
+// Radius-8 z pairs of one row from its whole tensor-memory ring v (slot p mod 16
+// holds signed plane p; slot S = vk mod 16): acc += w_l (q[vk + l] + q[vk - l]),
+// l = 1..8 ascending, q[vk + 8] being the entering qin.
+template <int S>
+__device__ __forceinline__ void z_pairs_r8(float2 &lo, float2 &hi, const float2 *wz2, const float4 (&v)[16],
+                                           const float4 qin)
+{
+#pragma unroll
+    for (int l = 1; l <= 8; ++l) {
+        const float4 up = l == 8 ? qin : v[(S + l) & 15];
+        const float4 dn = v[(S - l + 16) & 15];
+        lo = __ffma2_rn(wz2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo);
+        hi = __ffma2_rn(wz2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi);
+    }
+}
+
 // One CTA's work: tile (bx, by), z chunk bz, of the step u^n -> u^{n+1}.
 // tm_cur maps u^n with the halo box (ring A), tm_ctile u^n with the tile box
 // (the z-queue entries in ring B), tm_prev and tm_kappa the other ring B tiles.
@@ -456,7 +472,26 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 mbar_arrive(&emptyB[sb]);
             }
             // z pairs from the tensor-memory queues
-            {
+            if constexpr (R == 8) {
+                // per row, the whole 16-slot ring in one load from a fixed address,
+                // then pairs l = 1..8 at slots (vk + l) and (vk - l) mod 16, selected
+                // through a switch on vk mod 16 (vk + 8 is the entering one)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    float4 v[16];
+                    __syncwarp();
+                    tmem_ld_ring(tl + C::QC * e, v);
+                    switch (vk & 15) {
+#define FD_ZP(S) \
+    case S: z_pairs_r8<S>(lo[e], hi[e], a.wz2, v, qin[e]); break;
+                        FD_ZP(0) FD_ZP(1) FD_ZP(2) FD_ZP(3) FD_ZP(4) FD_ZP(5) FD_ZP(6) FD_ZP(7)
+                        FD_ZP(8) FD_ZP(9) FD_ZP(10) FD_ZP(11) FD_ZP(12) FD_ZP(13) FD_ZP(14) FD_ZP(15)
+#undef FD_ZP
+                    }
+                }
+                const uint32_t cs = tl + 4 * (uint32_t)((vk + R) & (C::QS - 1));
+                tmem_st4_2(cs, qin[0], cs + C::QC, qin[1]);
+            } else {
                 // per row, pairs l = 1..4 then 5..8: signed indices vk + l and vk - l
                 // from their slots (vk + 8 is the entering one; its slot still holds
                 // vk - 8)
