@@ -179,17 +179,18 @@ __device__ __forceinline__ void update_row(const IsoArgs &a, float *prev, const 
     }
 }
 
-// Radius-8 z pairs of one row from its whole tensor-memory ring v (slot p mod 16
-// holds signed plane p; slot S = vk mod 16): acc += w_l (q[vk + l] + q[vk - l]),
-// l = 1..8 ascending, q[vk + 8] being the entering qin.
-template <int S>
-__device__ __forceinline__ void z_pairs_r8(float2 &lo, float2 &hi, const float2 *wz2, const float4 (&v)[16],
-                                           const float4 qin)
+// z pairs of one row from its whole tensor-memory ring v of 2R slots (slot p mod
+// 2R holds signed plane p; slot S = vk mod 2R): acc += w_l (q[vk + l] + q[vk - l]),
+// l = 1..R ascending, q[vk + R] being the entering qin.
+template <int R, int S>
+__device__ __forceinline__ void z_pairs_ring(float2 &lo, float2 &hi, const float2 *wz2, const float4 (&v)[2 * R],
+                                             const float4 qin)
 {
+    constexpr int M = 2 * R - 1;   // ring slots - 1
 #pragma unroll
-    for (int l = 1; l <= 8; ++l) {
-        const float4 up = l == 8 ? qin : v[(S + l) & 15];
-        const float4 dn = v[(S - l + 16) & 15];
+    for (int l = 1; l <= R; ++l) {
+        const float4 up = l == R ? qin : v[(S + l) & M];
+        const float4 dn = v[(S - l + 2 * R) & M];
         lo = __ffma2_rn(wz2[l], __fadd2_rn(make_float2(up.x, up.y), make_float2(dn.x, dn.y)), lo);
         hi = __ffma2_rn(wz2[l], __fadd2_rn(make_float2(up.z, up.w), make_float2(dn.z, dn.w)), hi);
     }
@@ -472,18 +473,21 @@ __device__ __forceinline__ void iso_body(const CUtensorMap *tm_cur, const CUtens
                 mbar_arrive(&emptyB[sb]);
             }
             // z pairs from the tensor-memory queues
-            if constexpr (R == 8) {
-                // per row, the whole 16-slot ring in one load from a fixed address,
-                // then pairs l = 1..8 at slots (vk + l) and (vk - l) mod 16, selected
-                // through a switch on vk mod 16 (vk + 8 is the entering one)
+            if constexpr (R == 8 || R == 4) {
+                // per row, the whole ring of 2R slots in one load from a fixed
+                // address, then pairs l = 1..R at slots (vk + l) and (vk - l) mod 2R,
+                // selected through a switch on vk mod 2R (vk + R is the entering one)
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    float4 v[16];
+                    float4 v[2 * R];
                     __syncwarp();
-                    tmem_ld_ring(tl + C::QC * e, v);
-                    switch (vk & 15) {
+                    if constexpr (R == 8)
+                        tmem_ld_ring(tl + C::QC * e, v);
+                    else
+                        tmem_ld_ring8(tl + C::QC * e, v);
+                    switch (vk & (2 * R - 1)) {
 #define FD_ZP(S) \
-    case S: z_pairs_r8<S>(lo[e], hi[e], a.wz2, v, qin[e]); break;
+    case S: z_pairs_ring<R, (S) & (2 * R - 1)>(lo[e], hi[e], a.wz2, v, qin[e]); break;
                         FD_ZP(0) FD_ZP(1) FD_ZP(2) FD_ZP(3) FD_ZP(4) FD_ZP(5) FD_ZP(6) FD_ZP(7)
                         FD_ZP(8) FD_ZP(9) FD_ZP(10) FD_ZP(11) FD_ZP(12) FD_ZP(13) FD_ZP(14) FD_ZP(15)
 #undef FD_ZP
