@@ -261,7 +261,8 @@ int fd_field(fd_grid_t *g, int which, float **dev_ptr, int *pitch);
  * 32 x 32 (lookahead 2, 3); radius 8: 64 x 8 (lookahead 2, 3), 32 x 16,
  * 32 x 32 (lookahead 2); VTI (12, 8): 64 x 8 (lookahead 2, 3), 32 x 16,
  * 32 x 32 (lookahead 2).  32 x 32 tiles keep the z queues in tensor memory.
- * A new grid starts with 32 x 32, lookahead 3 (isotropic radius 4), 32 x 32,
+ * A new grid starts with 32 x 32, lookahead 3 (isotropic radius 4; 64 x 16,
+ * lookahead 3 on a grid too small to fill the GPU with 32 x 32 CTAs), 32 x 32,
  * lookahead 2 (radius 8; VTI at R_z = 8) or 64 x 8, lookahead 2 (other VTI
  * radii), and a z chunk fitted to whole waves of the CTAs the GPU holds at
  * once: 32-96 planes (isotropic), 32-64 (VTI).
