@@ -16,6 +16,7 @@
 
 #include "coeffs.h"
 #include "fd_internal.h"
+#include "launch_policy.h"
 
 using namespace fdk;
 
@@ -89,7 +90,7 @@ void compute_layout(const fd_desc *d, fd_layout_t *L)
 
 Launch default_launch(const fd_desc *d)
 {
-    return d->mode == FD_MODE_ISO ? iso_default_launch(d->r_xy, d->nx, d->ny, d->nz)
+    return d->mode == FD_MODE_ISO ? iso_grid_launch(d->r_xy, d->nx, d->ny, d->nz)
                                   : vti_default_launch(d->r_xy, d->r_z, d->nx, d->ny, d->nz);
 }
 

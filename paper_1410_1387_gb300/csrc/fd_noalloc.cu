@@ -42,6 +42,7 @@
 #include "coeffs.h"
 #include "fd.h"
 #include "fd_internal.h"
+#include "launch_policy.h"
 
 namespace fdk {
 int set_last_error(int code, const char *msg);
@@ -200,7 +201,7 @@ extern "C" int fd_iso_step_static(const fd_desc *d, const float *u_cur, float *u
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e, "scratch fill launch");
 
-    const Launch L = iso_default_launch(R, d->nx, d->ny, d->nz);
+    const Launch L = iso_grid_launch(R, d->nx, d->ny, d->nz);
     IsoMaps tm;
     int cr = encode_field_map(&tm.cur, u_cur, d->nx, d->ny, d->nz, lay.pitch, L.tx + 2 * R, L.ty + 2 * R);
     if (!cr) cr = encode_field_map(&tm.prev, u_prev, d->nx, d->ny, d->nz, lay.pitch, L.tx, L.ty);

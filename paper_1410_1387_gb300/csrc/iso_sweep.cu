@@ -904,21 +904,11 @@ Launch iso_default_launch(int R, int nx, int ny, int nz)
     if (R == 4) {
         // three CTAs of 32 x 32 per SM, z queues in tensor memory, two rows per
         // thread (512^3: 401.7 vs 394.6 Gpts/s for the one-row 64 x 16 form,
-        // interleaved in one process), when the grid fills the GPU's CTA slots at
-        // the shortest chunks; a smaller grid runs the one-row 64 x 16 form, whose
-        // CTAs have 288 threads for the same 1024 columns
+        // interleaved in one process)
         L.tx = 32;
         L.ty = 32;
         L.lookahead = 3;
-        const long slots = (long)device_sm_count() * IsoCfg<4, 32, 32, 3>::MINB;
-        const long most = (long)((nx + 31) / 32) * ((ny + 31) / 32) * ((nz + 31) / 32);
-        if (most >= slots) {
-            L.zchunk = wave_zchunk(L, nx, ny, nz, slots, 2 * R);
-        } else {
-            L.tx = 64;
-            L.ty = 16;
-            L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<4, 64, 16, 3>::MINB, 2 * R);
-        }
+        L.zchunk = wave_zchunk(L, nx, ny, nz, (long)device_sm_count() * IsoCfg<4, 32, 32, 3>::MINB, 2 * R);
     } else {
         // two CTAs of 32 x 32 per SM (z queues in tensor memory, two rows per thread)
         L.tx = 32;
