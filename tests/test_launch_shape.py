@@ -61,3 +61,59 @@ def test_wave_zchunk_ends_and_stays_in_bounds(tmp_path):
     assert one == 1
     assert c320 == 54                     # 6 chunks of 5 x 20 tiles: 600 CTAs, two waves of 304
     assert vti == 64                      # 8 chunks: 2048 CTAs, 6.7 waves of 304
+
+
+POLICY = r"""
+#include "launch_policy.h"
+#include <cstdio>
+namespace fdk {
+// the sweep's own default, as iso_sweep.cu gives it (32 x 32 tiles)
+Launch iso_default_launch(int R, int nx, int ny, int nz)
+{
+    Launch L{32, 32, 0, R == 4 ? 3 : 2};
+    L.zchunk = wave_zchunk(L, nx, ny, nz, 456, 2 * R);
+    return L;
+}
+}
+int main()
+{
+    const int cubes[] = {96, 200, 224, 240, 256, 320, 512};
+    for (int n : cubes) {
+        const fdk::Launch L = fdk::iso_grid_launch(4, n, n, n);
+        printf("%d %d %d %d %d\n", n, L.tx, L.ty, L.zchunk, L.lookahead);
+    }
+    const fdk::Launch L8 = fdk::iso_grid_launch(8, 96, 96, 96);
+    printf("8 %d %d %d %d\n", L8.tx, L8.ty, L8.zchunk, L8.lookahead);
+    return 0;
+}
+"""
+
+
+def test_radius4_grid_launch_policy(tmp_path):
+    """The radius-4 default: the two-row 32 x 32 form when the grid's 32 x 32
+    tiles times ceil(nz / 32) reach the GPU's CTA slots (152 SMs x 3; the SM
+    count falls back to 152 without a GPU), else the one-row 64 x 16 form at
+    lookahead 3 with a z chunk in range; radius 8 keeps its own default."""
+    inc = _cuda_include()
+    lib = os.path.join(os.path.dirname(inc), "lib64")
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")) or not shutil.which("g++") \
+            or not os.path.exists(os.path.join(lib, "libcudart.so")):
+        pytest.skip("no CUDA headers, runtime or host compiler")
+    src = tmp_path / "pol.cpp"
+    src.write_text(POLICY)
+    exe = tmp_path / "pol"
+    b = subprocess.run(["g++", "-std=c++17", "-O1", "-I", os.path.join(ROOT, "paper_1410_1387_gb300", "csrc"),
+                        "-I", inc, str(src), "-o", str(exe), "-L", lib, "-lcudart", "-Wl,-rpath," + lib],
+                       capture_output=True, text=True)
+    assert b.returncode == 0, b.stderr[-2000:]
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60, env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert r.returncode == 0, r.stderr
+    rows = [list(map(int, l.split())) for l in r.stdout.split("\n") if l.strip()]
+    got = {row[0]: tuple(row[1:]) for row in rows[:-1]}
+    for n in (96, 200, 224):                   # 27, 343, 343 CTAs at most: below 456 slots
+        tx, ty, zc, la = got[n]
+        assert (tx, ty, la) == (64, 16, 3) and min(32, n) <= zc <= min(96, n)
+    for n in (240, 256, 320, 512):             # 512, 512, 1000, 4096: the two-row form
+        assert got[n][:2] == (32, 32) and got[n][3] == 3
+    assert got[512][2] == 74
+    assert rows[-1][1:3] == [32, 32] and rows[-1][4] == 2
