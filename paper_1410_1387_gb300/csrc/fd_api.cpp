@@ -922,15 +922,20 @@ int fd_run_to_host(fd_grid_t *g, int nsteps, float *host_dst, int chunk_steps)
         }
         CU(cudaEventRecord(g->copy_ev[i], g->stream), "event record");
     }
-    // ... then each chunk's rows once its steps are done
-    for (int i = 0; i < nchunks; ++i) {
+    // ... then each chunk's rows once its steps are done; copies already enqueued
+    // are waited for on every path, so none writes host_dst after the return
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nchunks && e == cudaSuccess; ++i) {
         const int ci = std::min(c, nsteps - i * c);
-        CU(cudaStreamWaitEvent(g->copy_stream, g->copy_ev[i], 0), "stream wait");
-        CU(cudaMemcpyAsync(host_dst + (size_t)i * c * g->nrec, g->trace + (size_t)(row0 + (long long)i * c) * g->nrec,
-                           (size_t)ci * g->nrec * sizeof(float), cudaMemcpyDeviceToHost, g->copy_stream),
-           "trace copy");
+        e = cudaStreamWaitEvent(g->copy_stream, g->copy_ev[i], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_dst + (size_t)i * c * g->nrec,
+                                g->trace + (size_t)(row0 + (long long)i * c) * g->nrec,
+                                (size_t)ci * g->nrec * sizeof(float), cudaMemcpyDeviceToHost, g->copy_stream);
     }
-    CU(cudaStreamSynchronize(g->copy_stream), "copy stream synchronize");
+    const cudaError_t es = cudaStreamSynchronize(g->copy_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "trace copy");
+    if (es != cudaSuccess) return cuda_fail(es, "copy stream synchronize");
     return check_dev_status(g);
 }
 
